@@ -186,7 +186,7 @@ int orc_floyd_from_draws(int n_s, int p, const int32_t *draws, int32_t *out)
 /* ------------------------------------------------------------------------- */
 /* Thermostat noise (Sec. 2, Eq. (2)): three standard normals per particle and
  * step from stream 1, by the Box-Muller transform of four words
- * a_k = ((w_k >> 8) + 1/2) 2^-24:
+ * a_k = ((w_k >> 9) + 1/2) 2^-23 (exactly representable in binary32 and FP64):
  *   xi_x = sqrt(-2 ln a0) cos(2 pi a1), xi_y = sqrt(-2 ln a0) sin(2 pi a1),
  *   xi_z = sqrt(-2 ln a2) cos(2 pi a3).                                          */
 /* ------------------------------------------------------------------------- */
@@ -195,7 +195,7 @@ void orc_gaussians(uint64_t seed, uint64_t step, uint32_t tag, double out[3])
     word_stream ws;
     ws_init(&ws, seed, step, tag, 1u);
     double a[4];
-    for (int k = 0; k < 4; ++k) a[k] = ((double)(ws_next(&ws) >> 8) + 0.5) * (1.0 / 16777216.0);
+    for (int k = 0; k < 4; ++k) a[k] = ((double)(ws_next(&ws) >> 9) + 0.5) * (1.0 / 8388608.0);
     const double two_pi = 6.283185307179586476925286766559;
     double r0 = sqrt(-2.0 * log(a[0]));
     double r1 = sqrt(-2.0 * log(a[2]));
