@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark: particle-steps/s of the RBL step vs the full Verlet list on one GB300.
+
+Workload (default): LJ fluid N = 1,048,576 (FCC 64^3 x 4), rho* = 0.8, T* = 1.5,
+r_c = 1.5, r_s = 3.5, skin 0.3, p = 10, Langevin gamma = 1 (NVT), dt = 0.005,
+FP32 pair math with int64 fixed-point force sums, FP64 integration.  One "step" is
+one pass of the whole hot path: kick/drift/thermostat, device-conditional list
+rebuild (cell hash, counting sort, scan, permute, two-level list build), RBL force,
+force reduction.  Inputs are synthetic (seeded FCC start + Maxwell-Boltzmann).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on the host
+cores on the same workload (the paper's own implementation is unpublished).
+Multi-GPU: independent replicas (one per rank, seed 1 + rank), weak scaling, no
+collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s, RBL vs full Verlet list on 1 GB300 at matched pressure/g(r)"
+WORKLOAD = dict(name="lj_fluid_N1048576_rho0.8_T1.5_rc1.5_rs3.5_skin0.3_p10_nvt", N=1048576, rho=0.8, T=1.5,
+                rc=1.5, rs=3.5, skin=0.3, p=10, dt=0.005, gamma=1.0, K=2)
+FORCE_KERNEL = "k_force<0, true, false>"  # RBL, FP32, no energy
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-full-list", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="override particle count (debug only)")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(N):
+    """DRAM bytes per launch of the force kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        from paper_2105_04884_gb300 import _build
+
+        if d.get("source_sha") != _build.source_digest():
+            return None
+        return float(d["dram_bytes_per_particle"]) * N
+    except Exception:
+        return None
+
+
+def make_workload(N, seed):
+    from paper_2105_04884_gb300 import inputs
+
+    w = WORKLOAD
+    x, L = inputs.fcc(N, w["rho"], 0.01, seed=seed)
+    v = inputs.maxwell_boltzmann(N, w["T"], seed=seed)
+    return x, v, L
+
+
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2105_04884_gb300 import rbl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOAD
+    N = a.N
+    x, v, L = make_workload(N, 1 + rank)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def max_over_ranks(t):
+        if world == 1:
+            return t
+        import torch.distributed as dist
+
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    def timed(system, K, phases=True):
+        system.set_phase_timing(phases)
+        system.phase_times(reset=True)
+        stream = system.stream
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        system.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        return max_over_ranks(ms), system.phase_times()
+
+    common = dict(r_c=w["rc"], r_s=w["rs"], skin=w["skin"], p=w["p"], dt=w["dt"], T=w["T"], gamma=w["gamma"],
+                  seed=1 + rank, cells_per_cutoff=w["K"], precision=rbl.RBL_FP32)
+    s = rbl.System(x, v, L, **common)
+    s.step(a.warmup)
+    obs0 = s.observables()
+    clocks = Clocks(local)
+    clocks.start()
+    ms, (phase_ms, nsteps) = timed(s, a.steps, phases=True)
+    clk = clocks.stop()
+    obs = s.observables()
+    value = N * a.steps * world / (ms * 1e-3)
+    # graph-replay timing of the same workload (no per-phase events)
+    ms_graph, _ = timed(s, a.steps, phases=False)
+    s.set_phase_timing(True)
+
+    # roofline of the force kernel (algorithmic bytes per particle)
+    nc, p = obs["Nc_mean"], w["p"]
+    alg_bytes_pp = 16 + 4 + 4 * nc + 4 + 4 * p + 24
+    t_force = phase_ms[2] / nsteps * 1e-3
+    achieved = alg_bytes_pp * N / t_force / 1e9
+    peak, peak_kind = load_peaks()
+    traffic = load_traffic(N)
+    result = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded FCC start + Maxwell-Boltzmann velocities)",
+        "config": {"workload": w["name"], "N": N, "rho": w["rho"], "T": w["T"], "r_c": w["rc"], "r_s": w["rs"],
+                   "skin": w["skin"], "p": p, "dt": w["dt"], "gamma": w["gamma"], "cells_per_cutoff": w["K"],
+                   "pair_math": "fp32 + int64 fixed-point sums", "integration": "fp64 BAOAB",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2 (lists %.0f MB)" % (4 * N * (nc + obs["Ns_mean"]) / 1e6),
+                   "timed_path": "direct launches with per-phase CUDA events"},
+        "gpu_launches": 14 * a.steps + 1,
+        "phases_ms_per_step": {"integrate": phase_ms[0] / nsteps, "rebuild_chain": phase_ms[1] / nsteps,
+                               "force_kernel": phase_ms[2] / nsteps, "force_reduce": phase_ms[3] / nsteps},
+        "graph_replay_ms_per_step": ms_graph / a.steps,
+        "rebuilds_in_timed_region": obs["n_rebuild"] - obs0["n_rebuild"],
+        "rows": {"core_mean": nc, "shell_mean": obs["Ns_mean"], "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"]},
+        "roofline": {"kernel": FORCE_KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_particle": alg_bytes_pp,
+                     "traffic": traffic, "traffic_per": "launch"},
+        "clocks": clk,
+    }
+    # full Verlet list on the same GPU and workload
+    if not a.no_full_list:
+        del s
+        torch.cuda.empty_cache()
+        sf = rbl.System(x, v, L, full_list=True, **common)
+        sf.step(a.warmup)
+        msf, (pmf, nf) = timed(sf, a.steps, phases=True)
+        vf = N * a.steps * world / (msf * 1e-3)
+        of = sf.observables()
+        result["full_list"] = {"value": vf, "ms_per_step": msf / a.steps,
+                               "force_kernel_ms": pmf[2] / nf, "full_mean": of["Ns_mean"]}
+        result["speedup_vs_full_list"] = value / vf
+        del sf
+        torch.cuda.empty_cache()
+    # end to end through the C ABI with host buffers: upload once, K x (step + scalar
+    # readback), download the final state
+    if not a.no_e2e:
+        import ctypes
+
+        se = rbl.System(x, v, L, **common)
+        se.set_phase_timing(False)
+        se.step(a.warmup)
+        xh = torch.from_numpy(x).pin_memory()
+        vh = torch.from_numpy(v).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        vo = torch.empty_like(vh).pin_memory()
+        obs_c = rbl.rbl_obs()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()), 0, 0))
+        for _ in range(a.steps):
+            se._check(se.lib.rbl_step(se.h, 1))
+            se._check(se.lib.rbl_observables(se.h, ctypes.byref(obs_c)))
+        step = ctypes.c_longlong()
+        se._check(se.lib.rbl_get_state(se.h, ctypes.c_void_p(xo.data_ptr()), ctypes.c_void_p(vo.data_ptr()),
+                                       ctypes.byref(step), 0))
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        result["e2e"] = {"value": N * a.steps * world / te, "unit": "particle-steps/s",
+                         "h2d_bytes_per_step": 48 * N / a.steps,
+                         "d2h_bytes_per_step": 48 * N / a.steps + 256,
+                         "path": "rbl_set_state(host) + steps x (rbl_step(1) + rbl_observables) + rbl_get_state(host)"}
+        del se
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(x, v, L, a.cpu_steps)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(x, v, L, steps):
+    import oracle
+
+    w = WORKLOAD
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    t0 = time.perf_counter()
+    oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, steps)
+    t = time.perf_counter() - t0
+    return {"value": len(x) * steps / t, "unit": "particle-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{steps} steps of the same N={len(x)} workload from its start (includes the initial list "
+                      f"build), FP64 C oracle with OpenMP"}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    import numpy as np  # noqa: F401
+
+    import oracle
+
+    w = WORKLOAD
+    N = a.N
+    x, v, L = make_workload(N, 1)
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    x, v, _, _ = oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, a.warmup)
+    t0 = time.perf_counter()
+    oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, a.steps,
+               step0=a.warmup)
+    t = time.perf_counter() - t0
+    value = N * a.steps / t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3 / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "N": N},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": f"{a.steps} timed steps of the full workload (lists "
+                                                         f"rebuilt at the start of the timed call)"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_info()
+    if a.impl == "reference":
+        res = run_reference(a, rank, world)
+    else:
+        res = run_ours(a, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * rbl.h -- C ABI of librbl, a GB300 (sm_103a) implementation of the random-batch
+ * list (RBL) short-range force step for Lennard-Jones molecular dynamics
+ * (Liang, Xu & Zhao, arXiv 2105.04884).
+ *
+ * Method (Sec. 2 of the paper): each particle keeps a core neighbour list
+ * (r < r_c) summed directly (Eq. (3)) and a shell list (r_c <= r < r_s) from which a
+ * random batch of p neighbours is drawn and scaled by N_s/p (Eq. (4)); the mean
+ * force is subtracted (Appendix A, F_cor) and the Langevin equation (Eq. (2)) is
+ * advanced with a velocity-Verlet splitting (Algorithm 1; Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Units: reduced LJ units, sigma = epsilon = m = k_B = 1.
+ *  - Particle arrays passed in or out are in TAG order (row t describes the particle
+ *    whose tag is t), AoS [N][3] doubles for positions/velocities/forces.  Inside the
+ *    context particles are kept in cell order; the library translates.
+ *  - "ptr_is_device": 0 means the pointer is host memory (the call copies through
+ *    the context's stream and synchronises), 1 means device memory on the context's
+ *    device (the call is asynchronous on the context's stream).
+ *  - Memory: the caller owns one device workspace of rbl_workspace_size() bytes
+ *    (any allocator; 256-byte aligned) and passes it to rbl_create; the context
+ *    carves every device array out of it and never allocates device memory itself.
+ *    The workspace must outlive the context.
+ *  - Streams: every kernel runs on the stream given to rbl_create (NULL = legacy
+ *    default stream).  Calls on one context must not run concurrently.
+ *  - Errors: every call returns an rbl_status; rbl_last_error() describes the last
+ *    failure on that context.  Device-side problems (row overflow, non-finite
+ *    positions, bounded waits that expired) are recorded in device flags and
+ *    reported by the next call that synchronises (rbl_step, rbl_forces with a host
+ *    pointer, rbl_observables, rbl_get_*).  No kernel traps.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter
+ *    (step_lo, step_hi, tag, stream<<24 | block), key (seed_lo, seed_hi); stream 0
+ *    draws the batches, stream 1 the thermostat noise.  Results therefore depend
+ *    only on (parameters, initial state, seed, step counter), never on launch
+ *    configuration.
+ */
+#ifndef RBL_H
+#define RBL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbl_ctx rbl_ctx;
+
+typedef enum {
+    RBL_OK = 0,
+    RBL_EINVAL = 1,      /* bad argument (message in rbl_last_error) */
+    RBL_ENOMEM = 2,      /* workspace too small */
+    RBL_EOVERFLOW = 3,   /* a list row or cell exceeded its capacity; recreate with larger caps */
+    RBL_ENONFINITE = 4,  /* a non-finite position, velocity or force was produced */
+    RBL_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    RBL_ECUDA = 6        /* a CUDA runtime call failed (message in rbl_last_error) */
+} rbl_status;
+
+enum { RBL_FP64 = 0, RBL_FP32 = 1 };
+
+typedef struct {
+    double L[3];          /* periodic box lengths; each >= 2 (r_s + skin) */
+    double r_c;           /* core radius: pairs r < r_c summed directly (Eq. (3)) */
+    double r_s;           /* cutoff radius: pairs r_c <= r < r_s sampled (Eq. (4)) */
+    double skin;          /* Verlet skin; lists rebuilt when a particle moved > skin/2 */
+    int p;                /* batch size, 1 <= p <= 64 */
+    double dt;            /* time step */
+    double T;             /* bath temperature (k_B T) */
+    double gamma;         /* Langevin friction; 0 = plain velocity-Verlet (NVE) */
+    unsigned long long seed;
+    int precision;        /* RBL_FP32: binary32 pair math, int64 fixed-point force sums;
+                             RBL_FP64: FP64 pair math and sums */
+    int full_list;        /* 1: classical cutoff with one full Verlet list (no batch) */
+    int subtract_net_force; /* 1 (default): subtract the mean force (Appendix A) */
+    int cells_per_cutoff; /* K: cell width >= (r_s + skin)/K, stencil (2K+1)^3; 1..3 */
+    int cap_core;         /* row capacities; 0 = derived from the density */
+    int cap_shell;        /* (shell row capacity, or full row capacity if full_list) */
+} rbl_params;
+
+typedef struct {
+    double U_est;         /* RBL energy estimate: 1/2 sum_i [sum_core u + s_i sum_B u] */
+    double W_est;         /* RBL virial estimate, same weights, W = sum r.f */
+    double K;             /* kinetic energy sum v^2 / 2 */
+    double T_kin;         /* 2K / (3N) */
+    double P;             /* rho T_kin + W_est / (3V) (no tail) */
+    double U_tail;        /* per-particle tail energy (8/3) pi rho (r_s^-9/3 - r_s^-3) */
+    double P_tail;        /* tail pressure (16/3) pi rho^2 (2 r_s^-9/3 - r_s^-3) */
+    double net_momentum[3];
+    long long step;       /* step counter */
+    long long n_rebuild;  /* list builds so far */
+    double Ns_mean;       /* mean shell (or full) row length at the last build */
+    double Nc_mean;       /* mean core row length at the last build */
+    int Ns_max;           /* longest shell (or full) row at the last build */
+    int Nc_max;           /* longest core row at the last build */
+} rbl_obs;
+
+/* Fills *prm with defaults: cells_per_cutoff 2, subtract_net_force 1, precision FP32,
+ * gamma 0, caps 0 (automatic).  Box, radii, p, dt, T, seed must still be set. */
+void rbl_params_default(rbl_params *prm);
+
+/* Bytes of device workspace a context for N particles with these parameters needs.
+ * Returns RBL_EINVAL for invalid parameters (see rbl_create). */
+rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes);
+
+/* Creates a context (host memory for the handle only).  Validates: N >= 2,
+ * 0 < r_c < r_s, skin >= 0, 1 <= p <= 64, dt > 0, T >= 0, gamma >= 0, finite values,
+ * every L_a >= 2 (r_s + skin), K in 1..3.  stream is a cudaStream_t (or NULL).
+ * The initial state is zero; load one with rbl_set_state. */
+rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,
+                      rbl_ctx **out);
+
+/* Loads positions x[N][3] (wrapped into [0, L)), velocities v[N][3] (may be NULL:
+ * zero) and the step counter; marks the lists stale.  Rejects non-finite input. */
+rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long long step, int ptr_is_device);
+
+/* Copies positions and velocities (either may be NULL) out in tag order, and the
+ * step counter (may be NULL). */
+rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, int ptr_is_device);
+
+/* Builds the cell list and the two-level neighbour lists from the current positions
+ * (Sec. 2: linked cells, core list r < r_c + skin, shell list
+ * max(r_c - skin, 0) <= r < r_s + skin; or the full list r < r_s + skin).
+ * rbl_step rebuilds by itself when needed; this forces a build now. */
+rbl_status rbl_build_lists(rbl_ctx *ctx);
+
+/* One force evaluation at the current positions with the batch drawn for the
+ * current step counter (Eqs. (3)-(4); mean force subtracted when enabled).
+ * F_out[N][3] in tag order (may be NULL: the force stays in the context), and the
+ * energy/virial estimates are refreshed for rbl_observables. Builds lists if stale. */
+rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device);
+
+/* Advances n >= 0 steps of Algorithm 1: velocity-Verlet kick/drift with the Langevin
+ * O-step between the drifts (BAOAB) when gamma > 0, list rebuild whenever some
+ * particle moved more than skin/2 since the last build, RBL force, final kick.
+ * Synchronises at the end and reports device flags. */
+rbl_status rbl_step(rbl_ctx *ctx, int n);
+
+/* Scalars of the current state (kinetic terms from the current velocities, energy
+ * and virial from the last force evaluation).  Synchronises. */
+rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
+
+/* Parity hooks.  kind 0 = core rows, 1 = shell rows (full rows when full_list).
+ * rows[N][cap] receives neighbour TAGS in the canonical row order (stencil slot of
+ * the neighbour's cell, then tag), counts[N] the lengths; host pointers.  Rows
+ * longer than cap return RBL_EOVERFLOW. Builds lists if stale. */
+rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts);
+
+/* The batch B(i) the force would use at step counter `step` with the current
+ * lists: batch[N][p] neighbour tags in ascending row position, counts[N] = min(p,
+ * N_s); host pointers. */
+rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts);
+
+/* Pair-distance histogram for g(r) (Sec. 3): adds to hist[b] the number of ordered
+ * pairs i != j with r < r_s and floor(sqrt(r2) / dr) = b < nbins, each pair taken
+ * from the list that classifies it like the force does (core rows for r < r_c,
+ * shell rows for r_c <= r < r_s; full rows in full-list mode).  Requires
+ * nbins * dr <= r_s.  hist[nbins] int64, host pointer, accumulated (not cleared).
+ * Builds lists if stale. */
+rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
+
+/* Phase timing.  While enabled, rbl_step launches each step's phases directly (no
+ * graph replay) and brackets them with CUDA events on the context's stream:
+ * phase 0 = kick/drift/thermostat kernel, 1 = rebuild chain (device-conditional:
+ * near-empty when no rebuild is due), 2 = force kernel alone, 3 = force reduction.
+ * rbl_phase_times adds the elapsed milliseconds of every timed step since the last
+ * reset to ms[4] and reports the number of timed steps; reset = 1 clears them. */
+rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable);
+rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int reset);
+
+/* Releases the handle (the workspace stays the caller's). NULL is ignored. */
+void rbl_destroy(rbl_ctx *ctx);
+
+/* Text of the last error on ctx ("" if none); valid until the next call. */
+const char *rbl_last_error(const rbl_ctx *ctx);
+
+/* Short name of a status code. */
+const char *rbl_status_string(rbl_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBL_H */

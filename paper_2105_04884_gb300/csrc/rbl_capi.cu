@@ -1,0 +1,654 @@
+// rbl_capi.cu -- host side of the C ABI declared in include/rbl.h.
+//
+// The context lives in host memory; every device array is carved out of the
+// caller's workspace.  A step of Algorithm 1 is enqueued as: fused kick/drift/
+// thermostat kernel, the (device-conditional) rebuild chain, the force kernel and
+// its reduction.  The steady-state step is captured once in a CUDA graph and
+// replayed; the step counter lives in device memory so replays stay valid.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "rbl_internal.cuh"
+
+using namespace rbl;
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+struct Layout {
+    size_t off[32];
+    int n;
+    size_t total;
+    int cap_c, cap_s, ncell, n3[3], ntiles, nblk;
+    size_t staging_bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+void set_err(rbl_ctx *c, const char *fmt, ...)
+{
+    if (!c) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+}
+
+rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
+{
+#define BAD(...)                                   \
+    do {                                           \
+        if (err) snprintf(err, errlen, __VA_ARGS__); \
+        return RBL_EINVAL;                         \
+    } while (0)
+    if (!p) BAD("params is NULL");
+    if (N < 2) BAD("N must be >= 2 (got %d)", N);
+    const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma};
+    for (double v : vals)
+        if (!std::isfinite(v)) BAD("non-finite parameter");
+    if (!(p->r_c > 0.0 && p->r_c < p->r_s)) BAD("need 0 < r_c < r_s (got r_c=%g, r_s=%g)", p->r_c, p->r_s);
+    if (!(p->skin >= 0.0)) BAD("skin must be >= 0");
+    if (p->p < 1 || p->p > kMaxP) BAD("p must be in 1..%d (got %d)", kMaxP, p->p);
+    if (!(p->dt > 0.0)) BAD("dt must be > 0");
+    if (!(p->T >= 0.0) || !(p->gamma >= 0.0)) BAD("T and gamma must be >= 0");
+    if (p->cells_per_cutoff < 1 || p->cells_per_cutoff > 3) BAD("cells_per_cutoff must be 1..3");
+    if (p->precision != RBL_FP32 && p->precision != RBL_FP64) BAD("precision must be RBL_FP32 or RBL_FP64");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->L[a] >= 2.0 * (p->r_s + p->skin)))
+            BAD("box length L[%d]=%g is below 2 (r_s + skin) = %g", a, p->L[a], 2.0 * (p->r_s + p->skin));
+    if (p->cap_core < 0 || p->cap_shell < 0) BAD("capacities must be >= 0");
+    return RBL_OK;
+#undef BAD
+}
+
+Layout make_layout(const rbl_params *p, int N)
+{
+    Layout L{};
+    double V = p->L[0] * p->L[1] * p->L[2];
+    double rho = N / V;
+    double rcut = p->r_s + p->skin;
+    double lo = p->r_c - p->skin > 0.0 ? p->r_c - p->skin : 0.0;
+    double core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
+    double shell_mean = rho * 4.0 / 3.0 * kPi * (std::pow(rcut, 3) - std::pow(lo, 3));
+    double full_mean = rho * 4.0 / 3.0 * kPi * std::pow(rcut, 3);
+    auto cap_of = [&](double mean) { return round_up((int)std::ceil(1.6 * mean + 24.0), 8); };
+    L.cap_c = p->full_list ? 8 : (p->cap_core > 0 ? round_up(p->cap_core, 4) : cap_of(core_mean));
+    L.cap_s = p->cap_shell > 0 ? round_up(p->cap_shell, 4) : cap_of(p->full_list ? full_mean : shell_mean);
+    int K = p->cells_per_cutoff;
+    long long nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        int n = (int)std::floor(p->L[a] * (double)K / rcut);
+        if (n < 1) n = 1;
+        L.n3[a] = n;
+        nc *= n;
+    }
+    L.ncell = (int)nc;
+    L.ntiles = (L.ncell + 2047) / 2048;
+    L.nblk = (N + kBlock - 1) / kBlock;
+    size_t Nz = (size_t)N;
+    L.staging_bytes = 48 * Nz;
+    size_t batch_bytes = 4 * Nz * (size_t)(p->p + 1);
+    if (batch_bytes > L.staging_bytes) L.staging_bytes = batch_bytes;
+    if (L.staging_bytes < (size_t)L.nblk * 32) L.staging_bytes = (size_t)L.nblk * 32;
+    if (L.staging_bytes < (1u << 20)) L.staging_bytes = 1u << 20;
+    const size_t sizes[] = {
+        24 * Nz, 24 * Nz, 24 * Nz, 24 * Nz,         // x, x_alt, v, v_alt
+        4 * Nz, 4 * Nz,                             // tag, tag_alt
+        16 * Nz, 16 * Nz, 16 * Nz,                  // pos, pos_alt, ubuild
+        24 * Nz,                                    // F
+        4 * Nz, 4 * Nz,                             // cell, order
+        4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), // counts, start, fill
+        4 * ((size_t)L.ntiles + 1),                 // blocksums
+        4 * Nz * (size_t)L.cap_c, 4 * Nz,           // core, n_core
+        4 * Nz * (size_t)L.cap_s, 4 * Nz,           // shell, n_shell
+        64 * (size_t)L.nblk,                        // partials [nblk][8] doubles
+        sizeof(DevScalars),                         // scalars
+        L.staging_bytes,                            // staging
+    };
+    L.n = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    size_t o = 0;
+    for (int k = 0; k < L.n; ++k) {
+        L.off[k] = o;
+        o += align256(sizes[k]);
+    }
+    L.total = o;
+    return L;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_err(ctx, "%s failed: %s", #call, cudaGetErrorString(e_));                \
+            return RBL_ECUDA;                                                            \
+        }                                                                                \
+    } while (0)
+
+rbl_status read_scalars(rbl_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->h_sc, ctx->view.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RBL_OK;
+}
+
+rbl_status check_flags(rbl_ctx *ctx)
+{
+    rbl_status st = read_scalars(ctx);
+    if (st != RBL_OK) return st;
+    unsigned f = ctx->h_sc->flags;
+    if (f & (kFlagOverflow | kFlagCellOverflow)) {
+        set_err(ctx, "list row or cell over capacity (longest core row %d / cap %d, longest shell row %d / cap %d)",
+                ctx->h_sc->nc_max, ctx->view.cap_c, ctx->h_sc->ns_max, ctx->view.cap_s);
+        return RBL_EOVERFLOW;
+    }
+    if (f & kFlagNonFinite) {
+        set_err(ctx, "non-finite position or velocity");
+        return RBL_ENONFINITE;
+    }
+    if (f & kFlagRngLimit) {
+        set_err(ctx, "bounded-draw rejection limit reached");
+        return RBL_ETIMEOUT;
+    }
+    return RBL_OK;
+}
+
+rbl_status ensure_lists(rbl_ctx *ctx)
+{
+    if (ctx->lists_valid) return RBL_OK;
+    CK(launch_rebuild(ctx->view, ctx->n_scan_blocks, false, ctx->stream));
+    ctx->lists_valid = 1;
+    ctx->force_valid = 0;
+    return RBL_OK;
+}
+
+rbl_status ensure_force(rbl_ctx *ctx, bool energy)
+{
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    if (ctx->force_valid && (!energy || ctx->energy_valid)) return RBL_OK;
+    CK(launch_forces(ctx->view, 0, 0, energy, ctx->stream));
+    ctx->force_valid = 1;
+    ctx->energy_valid = energy || ctx->view.precision == RBL_FP64;
+    return RBL_OK;
+}
+
+// One steady-state step: kick(ck)+drift+O, conditional rebuild, force at n+1.
+// ev (optional): 5 events recorded at the phase boundaries.
+cudaError_t enqueue_step(rbl_ctx *ctx, double ck, bool energy, cudaEvent_t *ev = nullptr)
+{
+    cudaError_t e = cudaSuccess;
+    if (ev) e = cudaEventRecord(ev[0], ctx->stream);
+    if (e == cudaSuccess) e = launch_integrate(ctx->view, ck, true, ctx->stream);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], ctx->stream);
+    if (e == cudaSuccess) e = launch_rebuild(ctx->view, ctx->n_scan_blocks, true, ctx->stream);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], ctx->stream);
+    if (e == cudaSuccess) e = launch_force_kernel(ctx->view, 1, energy, ctx->stream);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], ctx->stream);
+    if (e == cudaSuccess) e = launch_force_finish(ctx->view, 1, energy, ctx->stream);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], ctx->stream);
+    return e;
+}
+
+rbl_status ensure_events(rbl_ctx *ctx, int steps)
+{
+    if (ctx->ev_cap >= steps) return RBL_OK;
+    int cap = steps < 64 ? 64 : steps;
+    cudaEvent_t *ev = (cudaEvent_t *)std::calloc((size_t)cap * 5, sizeof(cudaEvent_t));
+    if (!ev) return RBL_ENOMEM;
+    for (int k = 0; k < ctx->ev_cap * 5; ++k) ev[k] = ctx->ev[k];
+    for (int k = ctx->ev_cap * 5; k < cap * 5; ++k) CK(cudaEventCreate(&ev[k]));
+    std::free(ctx->ev);
+    ctx->ev = ev;
+    ctx->ev_cap = cap;
+    return RBL_OK;
+}
+
+rbl_status ensure_graph(rbl_ctx *ctx)
+{
+    if (ctx->graph_exec) return RBL_OK;
+    cudaGraph_t g = nullptr;
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    CK(cudaStreamBeginCapture(ctx->stream, mode));
+    cudaError_t e = enqueue_step(ctx, ctx->prm.dt, false);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_err(ctx, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return RBL_ECUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_err(ctx, "graph instantiate failed: %s", cudaGetErrorString(e));
+        return RBL_ECUDA;
+    }
+    ctx->graph_exec = ex;
+    return RBL_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void rbl_params_default(rbl_params *prm)
+{
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->p = 10;
+    prm->dt = 0.005;
+    prm->T = 1.0;
+    prm->seed = 1;
+    prm->precision = RBL_FP32;
+    prm->subtract_net_force = 1;
+    prm->cells_per_cutoff = 2;
+}
+
+rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes)
+{
+    if (!bytes) return RBL_EINVAL;
+    rbl_status st = validate(prm, N, nullptr, 0);
+    if (st != RBL_OK) return st;
+    *bytes = make_layout(prm, N).total;
+    return RBL_OK;
+}
+
+rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,
+                      rbl_ctx **out)
+{
+    if (!out) return RBL_EINVAL;
+    *out = nullptr;
+    rbl_ctx *ctx = new (std::nothrow) rbl_ctx();
+    if (!ctx) return RBL_ENOMEM;
+    rbl_status st = validate(prm, N, ctx->err, sizeof(ctx->err));
+    if (st != RBL_OK) {
+        // keep the handle so the caller can read the message; it holds no device state
+        *out = ctx;
+        return st;
+    }
+    Layout L = make_layout(prm, N);
+    if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) {
+        set_err(ctx, "workspace must be 256-byte aligned and at least %zu bytes (got %zu)", L.total,
+                workspace_bytes);
+        *out = ctx;
+        return workspace_bytes < L.total ? RBL_ENOMEM : RBL_EINVAL;
+    }
+    ctx->prm = *prm;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->nblk = L.nblk;
+    ctx->n_scan_blocks = L.ntiles;
+    ctx->step = 0;
+    ctx->h_sc = new DevScalars();
+    char *base = (char *)workspace;
+    View &v = ctx->view;
+    v.N = N;
+    v.p = prm->p;
+    v.K = prm->cells_per_cutoff;
+    v.cap_c = L.cap_c;
+    v.cap_s = L.cap_s;
+    v.full_list = prm->full_list ? 1 : 0;
+    v.precision = prm->precision;
+    v.subtract = prm->subtract_net_force ? 1 : 0;
+    v.ncell = L.ncell;
+    for (int a = 0; a < 3; ++a) {
+        int n = L.n3[a], K = prm->cells_per_cutoff;
+        v.n[a] = n;
+        if (n >= 2 * K + 1) {
+            v.nofs[a] = 2 * K + 1;
+            for (int o = 0; o < 2 * K + 1; ++o) v.ofs[a][o] = o - K;
+        } else {
+            v.nofs[a] = n;
+            for (int o = 0; o < n; ++o) v.ofs[a][o] = o;
+        }
+        v.L[a] = prm->L[a];
+        v.inv[a] = 4294967296.0 / prm->L[a];
+        v.h[a] = (float)(prm->L[a] / 4294967296.0);
+    }
+    double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
+    double lo = rc - sk > 0.0 ? rc - sk : 0.0;
+    v.t_core_list = (float)((rc + sk) * (rc + sk));
+    v.t_shell_lo = (float)(lo * lo);
+    v.t_cut_list = (float)((rs + sk) * (rs + sk));
+    v.t_rc2 = (float)(rc * rc);
+    v.t_rs2 = (float)(rs * rs);
+    v.t_disp = (float)(0.25 * sk * sk);
+    v.dt = prm->dt;
+    v.T = prm->T;
+    v.gamma = prm->gamma;
+    v.c1 = std::exp(-prm->gamma * prm->dt);
+    v.c2f = (float)std::sqrt((1.0 - v.c1 * v.c1) * prm->T);
+    v.seed = prm->seed;
+    int k = 0;
+    v.x = (double *)(base + L.off[k++]);
+    v.x_alt = (double *)(base + L.off[k++]);
+    v.v = (double *)(base + L.off[k++]);
+    v.v_alt = (double *)(base + L.off[k++]);
+    v.tag = (int *)(base + L.off[k++]);
+    v.tag_alt = (int *)(base + L.off[k++]);
+    v.pos = (int4 *)(base + L.off[k++]);
+    v.pos_alt = (int4 *)(base + L.off[k++]);
+    v.ubuild = (int4 *)(base + L.off[k++]);
+    v.F = (void *)(base + L.off[k++]);
+    v.cell = (int *)(base + L.off[k++]);
+    v.order = (int *)(base + L.off[k++]);
+    v.counts = (int *)(base + L.off[k++]);
+    v.start = (int *)(base + L.off[k++]);
+    v.fill = (int *)(base + L.off[k++]);
+    v.blocksums = (int *)(base + L.off[k++]);
+    v.core = (int *)(base + L.off[k++]);
+    v.n_core = (int *)(base + L.off[k++]);
+    v.shell = (int *)(base + L.off[k++]);
+    v.n_shell = (int *)(base + L.off[k++]);
+    v.partials = (double *)(base + L.off[k++]);
+    v.sc = (DevScalars *)(base + L.off[k++]);
+    v.staging = (double *)(base + L.off[k++]);
+    ctx->staging_bytes = L.staging_bytes;
+    cudaError_t e = cudaMemsetAsync(v.sc, 0, sizeof(DevScalars), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * (size_t)L.nblk, ctx->stream);
+    if (e != cudaSuccess) {
+        set_err(ctx, "initialisation failed: %s", cudaGetErrorString(e));
+        *out = ctx;
+        return RBL_ECUDA;
+    }
+    *out = ctx;
+    return RBL_OK;
+}
+
+rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long long step, int ptr_is_device)
+{
+    if (!ctx || !x || step < 0) return RBL_EINVAL;
+    size_t bytes = 24 * (size_t)ctx->view.N;
+    const double *dx = x, *dv = v;
+    if (!ptr_is_device) {
+        double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->view.N;
+        CK(cudaMemcpyAsync(sx, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        if (v) CK(cudaMemcpyAsync(sv, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        dx = sx;
+        dv = v ? sv : nullptr;
+    }
+    DevScalars z{};
+    *ctx->h_sc = z;
+    ctx->h_sc->step = (unsigned long long)step;
+    ctx->h_sc->n_rebuild = 0;
+    CK(cudaMemcpyAsync(ctx->view.sc, ctx->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_load_state(ctx->view, dx, dv, ctx->stream));
+    ctx->step = step;
+    ctx->lists_valid = 0;
+    ctx->force_valid = 0;
+    ctx->energy_valid = 0;
+    if (!ptr_is_device) {
+        rbl_status st = check_flags(ctx);
+        if (st != RBL_OK) return st;
+    }
+    return RBL_OK;
+}
+
+rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, int ptr_is_device)
+{
+    if (!ctx) return RBL_EINVAL;
+    if (step) *step = ctx->step;
+    if (!x && !v) return RBL_OK;
+    size_t bytes = 24 * (size_t)ctx->view.N;
+    if (ptr_is_device) {
+        CK(launch_store_state(ctx->view, x, v, ctx->stream));
+        return RBL_OK;
+    }
+    double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->view.N;
+    CK(launch_store_state(ctx->view, x ? sx : nullptr, v ? sv : nullptr, ctx->stream));
+    if (x) CK(cudaMemcpyAsync(x, sx, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (v) CK(cudaMemcpyAsync(v, sv, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RBL_OK;
+}
+
+rbl_status rbl_build_lists(rbl_ctx *ctx)
+{
+    if (!ctx) return RBL_EINVAL;
+    ctx->lists_valid = 0;
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    return check_flags(ctx);
+}
+
+rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device)
+{
+    if (!ctx) return RBL_EINVAL;
+    ctx->force_valid = 0;
+    rbl_status st = ensure_force(ctx, true);
+    if (st != RBL_OK) return st;
+    if (F_out) {
+        if (ptr_is_device) {
+            CK(launch_store_forces(ctx->view, F_out, ctx->stream));
+        } else {
+            CK(launch_store_forces(ctx->view, ctx->view.staging, ctx->stream));
+            CK(cudaMemcpyAsync(F_out, ctx->view.staging, 24 * (size_t)ctx->view.N, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            return check_flags(ctx);
+        }
+    }
+    return RBL_OK;
+}
+
+rbl_status rbl_step(rbl_ctx *ctx, int n)
+{
+    if (!ctx || n < 0) return RBL_EINVAL;
+    if (n == 0) return RBL_OK;
+    rbl_status st = ensure_force(ctx, false);
+    if (st != RBL_OK) return st;
+    // first step: opening half kick; middle steps: the closing and opening half
+    // kicks fused into one kick of dt (graph replay); last step also refreshes the
+    // energy/virial estimates.
+    if (ctx->phase_timing) {
+        st = ensure_events(ctx, n);
+        if (st != RBL_OK) return st;
+        for (int k = 0; k < n; ++k)
+            CK(enqueue_step(ctx, k == 0 ? 0.5 * ctx->prm.dt : ctx->prm.dt, k == n - 1, ctx->ev + 5 * k));
+        CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int k = 0; k < n; ++k)
+            for (int ph = 0; ph < 4; ++ph) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ctx->ev[5 * k + ph], ctx->ev[5 * k + ph + 1]));
+                ctx->phase_ms[ph] += ms;
+            }
+        ctx->phase_steps += n;
+        ctx->step += n;
+        ctx->force_valid = 1;
+        ctx->energy_valid = 1;
+        return check_flags(ctx);
+    }
+    CK(enqueue_step(ctx, 0.5 * ctx->prm.dt, n == 1));
+    if (n > 2) {
+        if (ctx->stream == nullptr) {
+            // the legacy default stream cannot be captured: launch directly
+            for (int k = 1; k < n - 1; ++k) CK(enqueue_step(ctx, ctx->prm.dt, false));
+        } else {
+            st = ensure_graph(ctx);
+            if (st != RBL_OK) return st;
+            for (int k = 1; k < n - 1; ++k) CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+        }
+    }
+    if (n > 1) CK(enqueue_step(ctx, ctx->prm.dt, true));
+    CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+    ctx->step += n;
+    ctx->force_valid = 1;
+    ctx->energy_valid = 1;
+    return check_flags(ctx);
+}
+
+rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out)
+{
+    if (!ctx || !out) return RBL_EINVAL;
+    rbl_status st = ensure_force(ctx, true);
+    if (st != RBL_OK) return st;
+    CK(launch_kinetic(ctx->view, ctx->stream));
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    const DevScalars &s = *ctx->h_sc;
+    const View &v = ctx->view;
+    double V = v.L[0] * v.L[1] * v.L[2];
+    double rho = v.N / V;
+    std::memset(out, 0, sizeof(*out));
+    out->U_est = s.energy;
+    out->W_est = s.virial;
+    out->K = 0.5 * s.ksum;
+    out->T_kin = s.ksum / (3.0 * v.N);
+    out->P = rho * out->T_kin + s.virial / (3.0 * V);
+    double rs = ctx->prm.r_s, i3 = 1.0 / (rs * rs * rs), i9 = i3 * i3 * i3;
+    out->U_tail = 8.0 / 3.0 * kPi * rho * (i9 / 3.0 - i3);
+    out->P_tail = 16.0 / 3.0 * kPi * rho * rho * (2.0 * i9 / 3.0 - i3);
+    for (int a = 0; a < 3; ++a) out->net_momentum[a] = s.psum[a];
+    out->step = (long long)s.step;
+    out->n_rebuild = s.n_rebuild;
+    out->Ns_mean = (double)s.ns_sum / v.N;
+    out->Nc_mean = (double)s.nc_sum / v.N;
+    out->Ns_max = s.ns_max;
+    out->Nc_max = s.nc_max;
+    return RBL_OK;
+}
+
+rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts)
+{
+    if (!ctx || !rows || !counts || (kind != 0 && kind != 1) || cap < 1) return RBL_EINVAL;
+    if (kind == 0 && ctx->view.full_list) return RBL_EINVAL;
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    const View &v = ctx->view;
+    size_t N = (size_t)v.N;
+    int rcap = kind == 0 ? v.cap_c : v.cap_s;
+    std::vector<int> tag(N), cnt(N), data(N * (size_t)rcap);
+    CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt.data(), kind == 0 ? v.n_core : v.n_shell, 4 * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(data.data(), kind == 0 ? v.core : v.shell, 4 * N * (size_t)rcap, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) {
+        int t = tag[i];
+        int n = cnt[i];
+        if (n > cap) {
+            set_err(ctx, "row of tag %d has %d entries, more than cap %d", t, n, cap);
+            return RBL_EOVERFLOW;
+        }
+        counts[t] = n;
+        for (int k = 0; k < n; ++k) rows[(size_t)t * cap + k] = tag[data[i * rcap + k]];
+    }
+    return RBL_OK;
+}
+
+rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
+{
+    if (!ctx || !batch || !counts || step < 0 || ctx->view.full_list) return RBL_EINVAL;
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    const View &v = ctx->view;
+    size_t N = (size_t)v.N;
+    int *dpos = (int *)v.staging;
+    int *dn = dpos + N * (size_t)v.p;
+    CK(launch_batch(v, (unsigned long long)step, dpos, dn, ctx->stream));
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    std::vector<int> tag(N), pos(N * (size_t)v.p), nb(N), ns(N), shell;
+    CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pos.data(), dpos, 4 * N * (size_t)v.p, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nb.data(), dn, 4 * N, cudaMemcpyDeviceToHost));
+    shell.resize(N * (size_t)v.cap_s);
+    CK(cudaMemcpy(shell.data(), v.shell, 4 * N * (size_t)v.cap_s, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) {
+        int t = tag[i];
+        int m = nb[i];
+        int *dst = batch + (size_t)t * v.p;
+        for (int q = 0; q < m; ++q) dst[q] = pos[i * v.p + q];
+        // ascending row position, then translate to neighbour tags
+        for (int a = 1; a < m; ++a) {
+            int x = dst[a], b = a - 1;
+            while (b >= 0 && dst[b] > x) {
+                dst[b + 1] = dst[b];
+                --b;
+            }
+            dst[b + 1] = x;
+        }
+        for (int q = 0; q < m; ++q) dst[q] = tag[shell[i * v.cap_s + dst[q]]];
+        counts[t] = m;
+    }
+    return RBL_OK;
+}
+
+rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist)
+{
+    if (!ctx || !hist || nbins < 1 || !(dr > 0.0f)) return RBL_EINVAL;
+    if ((double)nbins * dr > ctx->prm.r_s) {
+        set_err(ctx, "nbins * dr = %g exceeds r_s = %g", (double)nbins * dr, ctx->prm.r_s);
+        return RBL_EINVAL;
+    }
+    if ((size_t)nbins * 8 > ctx->staging_bytes) {
+        set_err(ctx, "too many bins for the staging area");
+        return RBL_EINVAL;
+    }
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    unsigned long long *dh = (unsigned long long *)ctx->view.staging;
+    CK(cudaMemsetAsync(dh, 0, 8 * (size_t)nbins, ctx->stream));
+    CK(launch_rdf(ctx->view, dr, nbins, dh, ctx->stream));
+    std::vector<unsigned long long> h(nbins);
+    CK(cudaMemcpyAsync(h.data(), dh, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, ctx->stream));
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    for (int b = 0; b < nbins; ++b) hist[b] += (long long)h[b];
+    return RBL_OK;
+}
+
+rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable)
+{
+    if (!ctx) return RBL_EINVAL;
+    ctx->phase_timing = enable ? 1 : 0;
+    return RBL_OK;
+}
+
+rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int reset)
+{
+    if (!ctx) return RBL_EINVAL;
+    if (ms)
+        for (int k = 0; k < 4; ++k) ms[k] = ctx->phase_ms[k];
+    if (steps) *steps = ctx->phase_steps;
+    if (reset) {
+        for (int k = 0; k < 4; ++k) ctx->phase_ms[k] = 0.0;
+        ctx->phase_steps = 0;
+    }
+    return RBL_OK;
+}
+
+void rbl_destroy(rbl_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    for (int k = 0; k < ctx->ev_cap * 5; ++k) cudaEventDestroy(ctx->ev[k]);
+    std::free(ctx->ev);
+    delete ctx->h_sc;
+    delete ctx;
+}
+
+const char *rbl_last_error(const rbl_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+const char *rbl_status_string(rbl_status s)
+{
+    switch (s) {
+    case RBL_OK: return "RBL_OK";
+    case RBL_EINVAL: return "RBL_EINVAL";
+    case RBL_ENOMEM: return "RBL_ENOMEM";
+    case RBL_EOVERFLOW: return "RBL_EOVERFLOW";
+    case RBL_ENONFINITE: return "RBL_ENONFINITE";
+    case RBL_ETIMEOUT: return "RBL_ETIMEOUT";
+    case RBL_ECUDA: return "RBL_ECUDA";
+    }
+    return "unknown";
+}
+
+} // extern "C"

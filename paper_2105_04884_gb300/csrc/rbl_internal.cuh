@@ -1,0 +1,313 @@
+// rbl_internal.cuh -- device-side building blocks and the context layout of librbl.
+//
+// Everything here is written for sm_103a.  Decisions that select a neighbour (which
+// side of a cutoff a pair falls on, which cell a particle is in, which batch is
+// drawn) are made with explicitly rounded intrinsics (__fmul_rn, __fadd_rn,
+// __int2float_rn) so that no compiler contraction can move a pair across a cutoff;
+// the same rules are stated independently by the CPU oracle in the test-suite.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rbl.h"
+
+namespace rbl {
+
+constexpr int kMaxP = 64;          // largest batch size
+constexpr int kCellCap = 64;       // cells up to this size are sorted in local memory
+constexpr int kBlock = 256;        // threads per block of the per-particle kernels
+constexpr int kMaxStencil = 7;     // offsets per axis for K <= 3
+
+// Device flags (bit positions in DevScalars::flags).
+enum : unsigned { kFlagOverflow = 1u, kFlagNonFinite = 2u, kFlagCellOverflow = 4u, kFlagRngLimit = 8u };
+
+// Scalars living in device memory (one instance in the workspace).
+struct DevScalars {
+    unsigned long long fsum_q[3];   // FP32 path: sum of fixed-point forces (mod 2^64)
+    double fcor[3];                 // mean force subtracted from every particle
+    double energy, virial;          // RBL estimates from the last evaluation
+    double ksum;                    // sum v^2 (on demand)
+    double psum[3];                 // sum v (on demand)
+    unsigned flags;                 // kFlag* bits
+    int rebuild;                    // 1 when lists must be rebuilt before the next force
+    int nc_max, ns_max;             // longest rows at the last build (even past capacity)
+    unsigned long long ns_sum;      // total shell (or full) entries at the last build
+    unsigned long long nc_sum;      // total core entries at the last build
+    long long n_rebuild;            // builds so far
+    unsigned long long step;        // step counter n (batch/noise counters)
+};
+
+// Kernel-visible view of a context (passed by value).
+struct View {
+    int N, p, K, cap_c, cap_s, full_list, precision, subtract;
+    int ncell, n[3], nofs[3], ofs[3][kMaxStencil];
+    double L[3], inv[3];            // inv = 2^32 / L
+    float h[3];                     // L / 2^32 in binary32
+    float t_core_list, t_shell_lo, t_cut_list, t_rc2, t_rs2, t_disp;
+    double dt, T, gamma, c1;
+    float c2f;                      // sqrt((1 - c1^2) T) in binary32
+    unsigned long long seed;
+    // state (cell order); [buffer][axis][N] for x and v
+    double *x, *v;                  // current buffer base (3 consecutive N-arrays each)
+    double *x_alt, *v_alt;          // other buffer (permutation target)
+    int *tag, *tag_alt;
+    int4 *pos, *pos_alt;            // (ux, uy, uz, tag) 32-bit fixed-point image
+    int4 *ubuild;                   // image at the last build
+    void *F;                        // [3][N]: int64 fixed point (FP32 path) or double
+    int *cell, *order;
+    int *counts, *start, *fill, *blocksums;
+    int *core, *n_core, *shell, *n_shell;
+    double *partials;               // [nblk][8]
+    DevScalars *sc;
+    double *staging;                // [2][N][3] doubles for host/device I/O
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): published multipliers and
+// Weyl key increments; ten rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Word stream for (seed, step, tag, stream): counter (step_lo, step_hi, tag,
+// stream<<24 | block), four words per block consumed in order.
+struct WordStream {
+    uint32_t k0, k1, s0, s1, tag, blk;
+    uint4 buf;
+    int pos;
+    __device__ __forceinline__ void init(unsigned long long seed, unsigned long long step, uint32_t t, uint32_t stream)
+    {
+        k0 = (uint32_t)seed;
+        k1 = (uint32_t)(seed >> 32);
+        s0 = (uint32_t)step;
+        s1 = (uint32_t)(step >> 32);
+        tag = t;
+        blk = stream << 24;
+        pos = 4;
+    }
+    __device__ __forceinline__ uint32_t next()
+    {
+        if (pos == 4) {
+            buf = philox4x32_10(make_uint4(s0, s1, tag, blk), k0, k1);
+            blk += 1u;
+            pos = 0;
+        }
+        uint32_t w = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
+        ++pos;
+        return w;
+    }
+};
+
+// Uniform integer in [0, s) (Lemire 2019, multiply-shift with rejection).  The
+// rejection loop is capped; hitting the cap (probability below (s/2^32)^64) sets a
+// flag instead of spinning.
+__device__ __forceinline__ uint32_t uniform_below(WordStream &ws, uint32_t s, unsigned *flags)
+{
+    unsigned long long m = (unsigned long long)ws.next() * s;
+    uint32_t low = (uint32_t)m;
+    if (low < s) {
+        uint32_t threshold = (0u - s) % s;
+        int guard = 0;
+        while (low < threshold) {
+            if (++guard > 64) {
+                atomicOr(flags, kFlagRngLimit);
+                break;
+            }
+            m = (unsigned long long)ws.next() * s;
+            low = (uint32_t)m;
+        }
+    }
+    return (uint32_t)(m >> 32);
+}
+
+// Floyd's sampling of p distinct positions in [0, ns) (Bentley & Floyd 1987), in
+// draw order; when ns <= p every position is taken.  Returns the count.
+__device__ __forceinline__ int floyd_positions(unsigned long long seed, unsigned long long step, int tag, int ns,
+                                               int p, int *S, unsigned *flags)
+{
+    if (ns <= p) {
+        for (int q = 0; q < ns; ++q) S[q] = q;
+        return ns;
+    }
+    WordStream ws;
+    ws.init(seed, step, (uint32_t)tag, 0u);
+    for (int q = 0; q < p; ++q) {
+        int k = ns - p + q;
+        int t = (int)uniform_below(ws, (uint32_t)k + 1u, flags);
+        bool seen = false;
+        for (int r = 0; r < q; ++r) seen |= (S[r] == t);
+        S[q] = seen ? k : t;
+    }
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// Canonical pair rule: d = (float)(int32)(u_i - u_j) * h, r2 = (dx dx + dy dy) + dz dz,
+// every operation rounded separately.
+// ---------------------------------------------------------------------------
+struct PairGeom {
+    float dx, dy, dz, r2;
+};
+
+__device__ __forceinline__ PairGeom pair_geom(int4 a, int4 b, const float h[3])
+{
+    PairGeom g;
+    g.dx = __fmul_rn(__int2float_rn((int)((unsigned)a.x - (unsigned)b.x)), h[0]);
+    g.dy = __fmul_rn(__int2float_rn((int)((unsigned)a.y - (unsigned)b.y)), h[1]);
+    g.dz = __fmul_rn(__int2float_rn((int)((unsigned)a.z - (unsigned)b.z)), h[2]);
+    g.r2 = __fadd_rn(__fadd_rn(__fmul_rn(g.dx, g.dx), __fmul_rn(g.dy, g.dy)), __fmul_rn(g.dz, g.dz));
+    return g;
+}
+
+// Cell coordinate along one axis: floor(u n / 2^32), exact.
+__device__ __forceinline__ int cell_coord(unsigned u, int n)
+{
+    return (int)(((unsigned long long)u * (unsigned)n) >> 32);
+}
+
+// LJ 12-6 in binary32: returns the force coefficient fmag with f = fmag * d, and
+// the pair energy / virial when asked.
+__device__ __forceinline__ float lj_coef(float r2, float *u, float *w)
+{
+    float inv = __frcp_rn(r2);
+    float r6 = __fmul_rn(__fmul_rn(inv, inv), inv);
+    float t = __fmaf_rn(2.0f, r6, -1.0f);         // 2 r^-6 - 1
+    float vir = __fmul_rn(__fmul_rn(24.0f, r6), t); // 24 (2 r^-12 - r^-6) = r . f
+    if (u) *u = __fmul_rn(__fmul_rn(4.0f, r6), __fadd_rn(r6, -1.0f));
+    if (w) *w = vir;
+    return __fmul_rn(vir, inv);
+}
+
+// ---------------------------------------------------------------------------
+// Exact fixed-point accumulation of binary32 values at scale 2^24.  Each value f
+// (|f| < 2^20) is split without rounding error into A = rint(4f) and
+// B = rint((4f - A) 2^22), so rint(f 2^24) = A 2^22 + B; A and B are summed as
+// 32-bit integers (order-independent, exact), using the 1.5 * 2^23 bias trick so
+// that both conversions are single binary32 operations.
+// ---------------------------------------------------------------------------
+struct FixedAcc {
+    unsigned a[3], b[3];
+    int n;
+    __device__ __forceinline__ void zero()
+    {
+        a[0] = a[1] = a[2] = b[0] = b[1] = b[2] = 0u;
+        n = 0;
+    }
+    __device__ __forceinline__ void add1(int k, float f)
+    {
+        const float M = 12582912.0f; // 1.5 * 2^23
+        float y = __fmaf_rn(f, 4.0f, M);
+        float hpart = __fsub_rn(y, M);
+        float r = __fmaf_rn(f, 4.0f, -hpart);
+        float z = __fmaf_rn(r, 4194304.0f, M);
+        a[k] += __float_as_uint(y);
+        b[k] += __float_as_uint(z);
+    }
+    __device__ __forceinline__ void add(float fx, float fy, float fz)
+    {
+        add1(0, fx);
+        add1(1, fy);
+        add1(2, fz);
+        ++n;
+    }
+    // Exact int64 value of the sum at scale 2^24 for component k.
+    __device__ __forceinline__ long long value(int k) const
+    {
+        const unsigned bias = 0x4B400000u; // bit pattern of 1.5 * 2^23
+        int A = (int)(a[k] - (unsigned)n * bias);
+        int B = (int)(b[k] - (unsigned)n * bias);
+        return (long long)A * 4194304LL + (long long)B;
+    }
+};
+
+constexpr double kFixedScale = 16777216.0;          // 2^24
+constexpr double kFixedInv = 1.0 / 16777216.0;
+
+// int64 -> double for |q| < 2^51 without the FP64 conversion unit: place q in the
+// mantissa of 1.5 * 2^52 and subtract that constant.
+__device__ __forceinline__ double i64_to_double(long long q)
+{
+    return __longlong_as_double(q + 0x4338000000000000LL) - 6755399441055744.0;
+}
+
+// binary32 -> FP64 by bit manipulation (normal numbers and zero; subnormals -> 0).
+__device__ __forceinline__ double f32_to_double(float f)
+{
+    unsigned b = __float_as_uint(f);
+    unsigned e = (b >> 23) & 0xffu;
+    unsigned long long r = (unsigned long long)(b >> 31) << 63;
+    if (e != 0u)
+        r |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)r);
+}
+
+// Fixed-point image of a coordinate x in [0, L): rint(x * 2^32/L) mod 2^32, the
+// product and the rounding taken as two separate FP64 operations.
+__device__ __forceinline__ unsigned quantize(double x, double inv)
+{
+    double t = __dmul_rn(x, inv);
+    double y = __dadd_rn(t, 6755399441055744.0); // 1.5 * 2^52: rounds to an integer
+    return (unsigned)(unsigned long long)__double_as_longlong(y);
+}
+
+// Wrap into [0, L) for a particle that moved by less than L.
+__device__ __forceinline__ double wrap(double x, double L)
+{
+    if (x < 0.0) x += L;
+    if (x >= L) x -= L;
+    return x;
+}
+
+inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
+
+} // namespace rbl
+
+// Host-side context (C ABI handle).
+struct rbl_ctx {
+    rbl_params prm;
+    rbl::View view;
+    cudaStream_t stream;
+    int nblk;
+    int n_scan_blocks;
+    int lists_valid;   // lists match the current positions
+    int force_valid;   // F matches the current positions and step counter
+    int energy_valid;  // energy/virial estimates match F
+    long long step;    // host mirror of the step counter
+    size_t staging_bytes;
+    cudaGraphExec_t graph_exec; // captured steady-state step
+    int phase_timing;           // rbl_set_phase_timing
+    cudaEvent_t *ev;            // 5 events per timed step
+    int ev_cap;                 // steps the event pool covers
+    double phase_ms[4];
+    long long phase_steps;
+    char err[512];
+    rbl::DevScalars *h_sc; // host mirror of the device scalars
+};
+
+// Kernel launchers implemented in the .cu files.
+namespace rbl {
+cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s);
+cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s);
+cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s);
+cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
+cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s);
+cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s);
+cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
+cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
+cudaError_t launch_kinetic(const View &v, cudaStream_t s);
+cudaError_t launch_batch(const View &v, unsigned long long step, int *out_pos, int *out_n, cudaStream_t s);
+cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
+} // namespace rbl

@@ -1,0 +1,238 @@
+// rbl_step.cu -- state I/O, the fused kick/drift/thermostat kernel and the
+// kinetic reductions (Algorithm 1; Sec. 2, Eq. (2); Sec. 3).
+//
+// Time stepping is velocity-Verlet for the underdamped Langevin equation in the
+// BAOAB splitting: B: v += dt/2 F~, A: x += dt/2 v, O: v = c1 v + c2 xi,
+// A: x += dt/2 v, force, B.  The closing B of one step and the opening B of the
+// next use the same force, so inside a multi-step call they are one kick of dt.
+// gamma = 0 gives plain velocity-Verlet (single drift of dt).  Positions, velocities
+// and the kicks are FP64; the thermostat noise xi is drawn in binary32 (Box-Muller
+// on Philox stream 1) and widened.  The kernel also refreshes the 32-bit
+// fixed-point image used by the pair rule and raises the rebuild flag when a
+// particle has moved more than skin/2 since the last build.
+#include "rbl_internal.cuh"
+
+namespace rbl {
+
+namespace {
+
+// Load AoS tag-ordered x (and v) into the SoA arrays (identity order), wrap x into
+// [0, L), refresh the fixed-point image, and flag non-finite input.
+__global__ void k_load(View v, const double *x, const double *vel)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    size_t N = (size_t)v.N;
+    unsigned u[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xa = x[(size_t)i * 3 + a];
+        double va = vel ? vel[(size_t)i * 3 + a] : 0.0;
+        bad |= !isfinite(xa) || !isfinite(va);
+        if (!isfinite(xa)) xa = 0.0;
+        xa = xa - v.L[a] * floor(xa / v.L[a]);
+        if (xa >= v.L[a]) xa -= v.L[a];
+        if (xa < 0.0) xa = 0.0;
+        v.x[a * N + i] = xa;
+        v.v[a * N + i] = va;
+        u[a] = quantize(xa, v.inv[a]);
+    }
+    v.tag[i] = i;
+    v.pos[i] = make_int4((int)u[0], (int)u[1], (int)u[2], i);
+    v.ubuild[i] = v.pos[i];
+    if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
+}
+
+// SoA cell-ordered state -> AoS tag-ordered output.
+__global__ void k_store(View v, double *x, double *vel)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    size_t N = (size_t)v.N;
+    size_t t = (size_t)v.tag[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (x) x[t * 3 + a] = v.x[a * N + i];
+        if (vel) vel[t * 3 + a] = v.v[a * N + i];
+    }
+}
+
+template <bool FP32>
+__device__ __forceinline__ double force_component(const View &v, int a, int i, double fcor)
+{
+    size_t N = (size_t)v.N;
+    if (FP32) {
+        long long q = ((const long long *)v.F)[a * N + i];
+        return fma(i64_to_double(q), kFixedInv, -fcor);
+    } else {
+        return ((const double *)v.F)[a * N + i] - fcor;
+    }
+}
+
+// ck: kick coefficient (dt/2 or dt).  DRIFT = false: kick only (closing half-kick).
+template <bool FP32, bool LANGEVIN, bool DRIFT>
+__global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= v.N) return;
+    size_t N = (size_t)v.N;
+    const DevScalars *sc = v.sc;
+    double vv[3], xx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = force_component<FP32>(v, a, i, sc->fcor[a]);
+        vv[a] = fma(ck, f, v.v[a * N + i]);
+    }
+    if constexpr (!DRIFT) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v.v[a * N + i] = vv[a];
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xx[a] = v.x[a * N + i];
+    int tag = v.tag[i];
+    if (LANGEVIN) {
+        const double half = 0.5 * v.dt;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xx[a] = fma(half, vv[a], xx[a]);
+        // O-step noise: Box-Muller of a_k = ((w_k >> 9) + 1/2) 2^-23, stream 1.
+        WordStream ws;
+        ws.init(v.seed, sc->step, (uint32_t)tag, 1u);
+        float av[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) av[k] = __fmul_rn(__fadd_rn((float)(ws.next() >> 9), 0.5f), 1.1920928955078125e-7f);
+        float r0 = sqrtf(-2.0f * logf(av[0]));
+        float r1 = sqrtf(-2.0f * logf(av[2]));
+        float s1, c1v;
+        sincospif(2.0f * av[1], &s1, &c1v);
+        float c3 = cospif(2.0f * av[3]);
+        float xi[3] = {r0 * c1v, r0 * s1, r1 * c3};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double noise = f32_to_double(v.c2f * xi[a]);
+            vv[a] = fma(v.c1, vv[a], noise);
+            xx[a] = fma(half, vv[a], xx[a]);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xx[a] = fma(v.dt, vv[a], xx[a]);
+    }
+    unsigned u[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double xa = wrap(xx[a], v.L[a]);
+        bad |= !(xa >= 0.0 && xa < v.L[a]) || !isfinite(vv[a]);
+        v.x[a * N + i] = xa;
+        v.v[a * N + i] = vv[a];
+        u[a] = quantize(xa, v.inv[a]);
+    }
+    int4 np = make_int4((int)u[0], (int)u[1], (int)u[2], tag);
+    v.pos[i] = np;
+    PairGeom g = pair_geom(np, v.ubuild[i], v.h);
+    if (g.r2 > v.t_disp) v.sc->rebuild = 1;
+    if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// sum v^2 and sum v: per-block partials (fixed order), then one block.
+__global__ void __launch_bounds__(kBlock) k_kinetic(View v)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    double x[4] = {0, 0, 0, 0};
+    if (i < v.N) {
+        size_t N = (size_t)v.N;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double va = v.v[a * N + i];
+            x[0] += va * va;
+            x[1 + a] = va;
+        }
+    }
+    __shared__ double sh[4][kBlock / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double s = wsum(x[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
+        v.staging[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_kinetic_finish(View v, int nblk)
+{
+    __shared__ double sh[4][32];
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += v.staging[(size_t)b * 4 + k];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double s = wsum(acc[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[4] = {0, 0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int k = 0; k < 4; ++k) tot[k] += sh[k][w];
+        v.sc->ksum = tot[0];
+        for (int a = 0; a < 3; ++a) v.sc->psum[a] = tot[1 + a];
+    }
+}
+
+} // namespace
+
+cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s)
+{
+    k_load<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s)
+{
+    k_store<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s)
+{
+    int g = ceil_div(v.N, kBlock);
+    bool fp32 = v.precision == RBL_FP32;
+    bool lang = v.gamma > 0.0;
+    if (!drift) {
+        if (fp32) k_integrate<true, false, false><<<g, kBlock, 0, s>>>(v, ck);
+        else k_integrate<false, false, false><<<g, kBlock, 0, s>>>(v, ck);
+    } else if (fp32) {
+        if (lang) k_integrate<true, true, true><<<g, kBlock, 0, s>>>(v, ck);
+        else k_integrate<true, false, true><<<g, kBlock, 0, s>>>(v, ck);
+    } else {
+        if (lang) k_integrate<false, true, true><<<g, kBlock, 0, s>>>(v, ck);
+        else k_integrate<false, false, true><<<g, kBlock, 0, s>>>(v, ck);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(const View &v, cudaStream_t s)
+{
+    int g = ceil_div(v.N, kBlock);
+    k_kinetic<<<g, kBlock, 0, s>>>(v);
+    k_kinetic_finish<<<1, 1024, 0, s>>>(v, g);
+    return cudaGetLastError();
+}
+
+} // namespace rbl

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of librbl (include/rbl.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies the device workspace
+and the stream.  If the library has not been built the first call raises -- there
+is no fallback path.
+
+    sys = System(x, v, L, r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005, T=1.5, gamma=1.0)
+    sys.step(100); obs = sys.observables(); F = sys.forces()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+RBL_FP64, RBL_FP32 = 0, 1
+STATUS = {0: "RBL_OK", 1: "RBL_EINVAL", 2: "RBL_ENOMEM", 3: "RBL_EOVERFLOW", 4: "RBL_ENONFINITE",
+          5: "RBL_ETIMEOUT", 6: "RBL_ECUDA"}
+
+
+class RblError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rbl_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("r_c", ctypes.c_double), ("r_s", ctypes.c_double),
+                ("skin", ctypes.c_double), ("p", ctypes.c_int), ("dt", ctypes.c_double), ("T", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int),
+                ("full_list", ctypes.c_int), ("subtract_net_force", ctypes.c_int),
+                ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_shell", ctypes.c_int)]
+
+
+class rbl_obs(ctypes.Structure):
+    _fields_ = [("U_est", ctypes.c_double), ("W_est", ctypes.c_double), ("K", ctypes.c_double),
+                ("T_kin", ctypes.c_double), ("P", ctypes.c_double), ("U_tail", ctypes.c_double),
+                ("P_tail", ctypes.c_double), ("net_momentum", ctypes.c_double * 3), ("step", ctypes.c_longlong),
+                ("n_rebuild", ctypes.c_longlong), ("Ns_mean", ctypes.c_double), ("Nc_mean", ctypes.c_double),
+                ("Ns_max", ctypes.c_int), ("Nc_max", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["net_momentum"] = list(self.net_momentum)
+        return d
+
+
+EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_create", "rbl_set_state", "rbl_get_state",
+           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_get_lists", "rbl_get_batch",
+           "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_destroy", "rbl_last_error",
+           "rbl_status_string"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load librbl.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"librbl is not built ({path}); run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    L.rbl_params_default.argtypes = [ctypes.POINTER(rbl_params)]
+    L.rbl_params_default.restype = None
+    L.rbl_workspace_size.argtypes = [ctypes.POINTER(rbl_params), I, ctypes.POINTER(ctypes.c_size_t)]
+    L.rbl_create.argtypes = [ctypes.POINTER(rbl_params), I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    L.rbl_set_state.argtypes = [P, P, P, LL, I]
+    L.rbl_get_state.argtypes = [P, P, P, ctypes.POINTER(LL), I]
+    L.rbl_build_lists.argtypes = [P]
+    L.rbl_forces.argtypes = [P, P, I]
+    L.rbl_step.argtypes = [P, I]
+    L.rbl_observables.argtypes = [P, ctypes.POINTER(rbl_obs)]
+    L.rbl_get_lists.argtypes = [P, I, P, I, P]
+    L.rbl_get_batch.argtypes = [P, LL, P, P]
+    L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
+    L.rbl_set_phase_timing.argtypes = [P, I]
+    L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
+    L.rbl_destroy.argtypes = [P]
+    L.rbl_destroy.restype = None
+    L.rbl_last_error.argtypes = [P]
+    L.rbl_last_error.restype = ctypes.c_char_p
+    L.rbl_status_string.argtypes = [I]
+    L.rbl_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("rbl_params_default", "rbl_destroy", "rbl_last_error", "rbl_status_string"):
+            getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32, full_list=False,
+                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_shell=0) -> rbl_params:
+    prm = rbl_params()
+    load().rbl_params_default(ctypes.byref(prm))
+    Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+    for a in range(3):
+        prm.L[a] = float(Lv[a])
+    prm.r_c, prm.r_s, prm.skin, prm.p = r_c, r_s, skin, int(p)
+    prm.dt, prm.T, prm.gamma, prm.seed = dt, T, gamma, int(seed)
+    prm.precision = int(precision)
+    prm.full_list = int(bool(full_list))
+    prm.subtract_net_force = int(bool(subtract_net_force))
+    prm.cells_per_cutoff = int(cells_per_cutoff)
+    prm.cap_core, prm.cap_shell = int(cap_core), int(cap_shell)
+    return prm
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class System:
+    """One RBL (or full-list) system on the current CUDA device and stream."""
+
+    def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
+                 full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_shell=0, step=0,
+                 stream=None, device=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load()
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
+        self.N = int(x.shape[0])
+        self.prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
+                               cells_per_cutoff, cap_core, cap_shell)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        # a stream of its own (the legacy default stream cannot host graph replays)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        size = ctypes.c_size_t()
+        self._check(self.lib.rbl_workspace_size(ctypes.byref(self.prm), self.N, ctypes.byref(size)))
+        self.workspace = torch.empty(int(size.value) + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = ctypes.c_void_p()
+        st = self.lib.rbl_create(ctypes.byref(self.prm), self.N, ctypes.c_void_p(aligned), int(size.value),
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        self.h = h
+        if st != 0:
+            msg = self.lib.rbl_last_error(h).decode() if h else ""
+            self.lib.rbl_destroy(h)
+            self.h = None
+            raise RblError(st, msg)
+        self.set_state(x, v, step)
+
+    # -- plumbing
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.rbl_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise RblError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rbl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _is_dev(a):
+        return hasattr(a, "data_ptr") and a.is_cuda
+
+    # -- C-ABI calls
+    def set_state(self, x, v=None, step=0):
+        dev = self._is_dev(x)
+        if dev:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+            v = None if v is None else np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        self._check(self.lib.rbl_set_state(self.h, _ptr(x), _ptr(v), int(step), int(dev)))
+
+    def get_state(self, device=False):
+        if device:
+            x = self._torch.empty((self.N, 3), dtype=self._torch.float64, device=self.device)
+            v = self._torch.empty_like(x)
+        else:
+            x = np.empty((self.N, 3))
+            v = np.empty((self.N, 3))
+        step = ctypes.c_longlong()
+        self._check(self.lib.rbl_get_state(self.h, _ptr(x), _ptr(v), ctypes.byref(step), int(device)))
+        if device:
+            self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return x, v, step.value
+
+    def build_lists(self):
+        self._check(self.lib.rbl_build_lists(self.h))
+
+    def forces(self, out=None):
+        if out is None:
+            out = np.empty((self.N, 3))
+        dev = self._is_dev(out)
+        self._check(self.lib.rbl_forces(self.h, _ptr(out), int(dev)))
+        if dev:
+            self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out
+
+    def step(self, n=1):
+        self._check(self.lib.rbl_step(self.h, int(n)))
+
+    def observables(self) -> dict:
+        o = rbl_obs()
+        self._check(self.lib.rbl_observables(self.h, ctypes.byref(o)))
+        return o.as_dict()
+
+    def get_lists(self, kind, cap=None):
+        if cap is None:
+            cap = int(self.observables()["Nc_max" if kind == 0 else "Ns_max"]) + 1
+        rows = np.full((self.N, cap), -1, np.int32)
+        counts = np.zeros(self.N, np.int32)
+        self._check(self.lib.rbl_get_lists(self.h, int(kind), _ptr(rows), int(cap), _ptr(counts)))
+        return rows, counts
+
+    def get_batch(self, step):
+        p = self.prm.p
+        batch = np.full((self.N, p), -1, np.int32)
+        counts = np.zeros(self.N, np.int32)
+        self._check(self.lib.rbl_get_batch(self.h, int(step), _ptr(batch), _ptr(counts)))
+        return batch, counts
+
+    def set_phase_timing(self, enable=True):
+        self._check(self.lib.rbl_set_phase_timing(self.h, int(bool(enable))))
+
+    def phase_times(self, reset=False):
+        """(ms per phase [integrate, rebuild, force kernel, force reduction], timed steps)."""
+        ms = (ctypes.c_double * 4)()
+        n = ctypes.c_longlong()
+        self._check(self.lib.rbl_phase_times(self.h, ms, ctypes.byref(n), int(bool(reset))))
+        return list(ms), n.value
+
+    def rdf(self, dr, nbins, hist=None):
+        if hist is None:
+            hist = np.zeros(nbins, np.int64)
+        self._check(self.lib.rbl_rdf(self.h, float(dr), int(nbins), _ptr(hist)))
+        return hist

@@ -1,0 +1,91 @@
+"""CPU checks of the C-ABI library: it builds, loads without a GPU, exports every
+function include/rbl.h declares, and validates parameters on the host."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2105_04884_gb300 import _build, rbl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rbl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbl_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return rbl.load()
+
+
+def test_exports_match_header(lib):
+    declared = _declared()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rbl_[a-z_]+)", out))
+    assert set(declared) <= exported, set(declared) - exported
+    assert sorted(rbl.EXPORTS) == declared
+    for name in declared:
+        getattr(lib, name)
+
+
+def test_params_default_and_status_strings(lib):
+    prm = rbl.rbl_params()
+    lib.rbl_params_default(ctypes.byref(prm))
+    assert prm.cells_per_cutoff == 2 and prm.subtract_net_force == 1 and prm.precision == rbl.RBL_FP32
+    for code, name in rbl.STATUS.items():
+        assert lib.rbl_status_string(code).decode() == name
+
+
+def _size(prm, N):
+    s = ctypes.c_size_t()
+    st = rbl.load().rbl_workspace_size(ctypes.byref(prm), N, ctypes.byref(s))
+    return st, s.value
+
+
+def test_workspace_size_and_validation(lib):
+    prm = rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005)
+    st, n1 = _size(prm, 1000)
+    assert st == 0 and n1 > 1000 * 200
+    st, n2 = _size(prm, 2000)
+    assert st == 0 and n2 > n1
+    bad = [
+        dict(r_c=3.5, r_s=1.5),                 # r_c >= r_s
+        dict(p=0), dict(p=65),                  # batch size range
+        dict(dt=0.0), dict(skin=-0.1),
+        dict(L=[7.0, 10.772, 10.772]),          # box below 2 (r_s + skin)
+        dict(cells_per_cutoff=4),
+        dict(T=float("nan")),
+    ]
+    for kw in bad:
+        args = dict(L=[10.772] * 3, r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005)
+        args.update(kw)
+        prm = rbl.make_params(**args)
+        assert _size(prm, 1000)[0] == 1, kw
+    assert _size(rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005), 1)[0] == 1  # N < 2
+
+
+def test_create_rejects_bad_workspace(lib):
+    prm = rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005)
+    h = ctypes.c_void_p()
+    st = lib.rbl_create(ctypes.byref(prm), 1000, None, 0, None, ctypes.byref(h))
+    assert st in (1, 2)
+    assert b"workspace" in lib.rbl_last_error(h)
+    lib.rbl_destroy(h)
+
+
+def test_product_has_no_oracle_dependency():
+    """The library and its binding never reach the CPU oracle."""
+    for sub in ("paper_2105_04884_gb300",):
+        for dirpath, _, files in os.walk(os.path.join(ROOT, sub)):
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h")):
+                    text = open(os.path.join(dirpath, f)).read()
+                    assert "import oracle" not in text and "from oracle" not in text, f
+                    assert "rbl_oracle" not in text, f

@@ -1,0 +1,146 @@
+"""GPU <-> oracle parity through the C ABI (librbl), on seeded LJ-fluid inputs.
+
+Bars (each stated where it is asserted):
+- cell/list membership and canonical row order: bit-exact;
+- sampled batches: bit-exact (same Philox stream, same Floyd draws);
+- forces: relative global norm ||F_gpu - F_orc|| / ||F_orc|| <= 1e-12 (FP64 path)
+  and <= 1e-5 (FP32 path);
+- FP32-path identities that hold exactly in fixed point: p >= max N_s reproduces the
+  full-list force bit for bit, and the full-list total force is exactly zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_04884_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2105_04884_gb300 import rbl  # noqa: E402
+
+CASES = {
+    # the N=1000 parity workload: rho* = 0.8, FCC + 0.01 jitter, r_c 1.5, r_s 3.5, skin 0.3, p 10
+    "n1000": dict(N=1000, rho=0.8, jitter=0.01, rc=1.5, rs=3.5, skin=0.3, p=10, K=2, seed=1),
+    # 2 cells per axis (stencil de-duplicated), disordered
+    "n1000_K1": dict(N=1000, rho=0.8, jitter=0.2, rc=1.5, rs=3.5, skin=0.3, p=10, K=1, seed=2),
+    # 4 < 2K+1 cells per axis at K = 2
+    "n500_small_box": dict(N=500, rho=0.8, jitter=0.3, rc=1.5, rs=3.5, skin=0.3, p=10, K=2, seed=3),
+    # ragged tail (N not a multiple of the block), r_c = 1.2, dense
+    "n4001_rc1.2": dict(N=4001, rho=0.8442, jitter=0.25, rc=1.2, rs=3.5, skin=0.3, p=5, K=2, seed=4),
+    # r_c = 2.0, p = 20, K = 3 (7^3 stencil)
+    "n3000_rc2_K3": dict(N=3000, rho=0.7, jitter=0.3, rc=2.0, rs=3.5, skin=0.3, p=20, K=3, seed=5),
+    # p = 1
+    "n2000_p1": dict(N=2000, rho=0.8, jitter=0.3, rc=1.5, rs=3.5, skin=0.3, p=1, K=2, seed=6),
+}
+
+
+def _state(c):
+    x, L = inputs.fcc(c["N"], c["rho"], c["jitter"], seed=c["seed"])
+    v = inputs.maxwell_boltzmann(c["N"], 1.5, seed=c["seed"])
+    return x, v, L
+
+
+def _system(c, x, v, L, **kw):
+    args = dict(r_c=c["rc"], r_s=c["rs"], skin=c["skin"], p=c["p"], dt=0.005, T=1.5, gamma=0.0, seed=c["seed"],
+                cells_per_cutoff=c["K"])
+    args.update(kw)
+    return rbl.System(x, v, L, **args)
+
+
+def _relnorm(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    c = CASES[request.param]
+    x, v, L = _state(c)
+    lists = oracle.build_lists(x, L, c["rc"], c["rs"], c["skin"], K=c["K"], method="cells")
+    return c, x, v, L, lists
+
+
+def test_lists_bit_exact(case):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L)
+    for kind, name in ((0, "core"), (1, "shell")):
+        rows, counts = s.get_lists(kind)
+        assert np.array_equal(counts, getattr(lists, "n_" + name)), name
+        for i in range(c["N"]):
+            assert np.array_equal(rows[i, : counts[i]], lists.row(name, i)), (name, i)
+
+
+def test_full_list_bit_exact(case):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L, full_list=True)
+    rows, counts = s.get_lists(1)
+    assert np.array_equal(counts, lists.n_full)
+    for i in range(c["N"]):
+        assert np.array_equal(rows[i, : counts[i]], lists.row("full", i))
+
+
+@pytest.mark.parametrize("step", [0, 1, 977])
+def test_batches_bit_exact(case, step):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L)
+    batch, counts = s.get_batch(step)
+    _, _, ob, obn = oracle.rbl_forces(x, L, c["rc"], c["rs"], c["skin"], c["p"], c["seed"], step, lists,
+                                      want_batch=True)
+    assert np.array_equal(counts, obn)
+    for i in range(c["N"]):
+        assert np.array_equal(batch[i, : counts[i]], ob[i, : obn[i]]), i
+
+
+@pytest.mark.parametrize("precision,tol", [(rbl.RBL_FP64, 1e-12), (rbl.RBL_FP32, 1e-5)])
+def test_forces_and_estimates(case, precision, tol):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L, precision=precision)
+    F = s.forces()
+    Fo, ev, _, _ = oracle.rbl_forces(x, L, c["rc"], c["rs"], c["skin"], c["p"], c["seed"], 0, lists)
+    Fo = oracle.subtract_mean(Fo)
+    assert _relnorm(F, Fo) <= tol
+    obs = s.observables()
+    assert abs(obs["U_est"] - ev[0]) <= tol * abs(ev[0]) * 10
+    assert abs(obs["W_est"] - ev[1]) <= tol * abs(ev[1]) * 10
+
+
+@pytest.mark.parametrize("precision,tol", [(rbl.RBL_FP64, 1e-12), (rbl.RBL_FP32, 1e-5)])
+def test_full_list_forces(case, precision, tol):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L, precision=precision, full_list=True)
+    F = s.forces()
+    Fo, ev = oracle.full_forces(x, L, c["rs"], lists)
+    assert _relnorm(F, oracle.subtract_mean(Fo)) <= tol
+    obs = s.observables()
+    assert abs(obs["U_est"] - ev[0]) <= tol * abs(ev[0]) * 10
+
+
+@pytest.mark.parametrize("N,rho,seed", [(1000, 0.8, 11), (2501, 0.9, 12), (800, 0.6, 13)])
+def test_fp32_identities_exact(N, rho, seed):
+    """Fixed-point sums are exact: p >= max N_s gives the full-list force bit for bit,
+    and the full-list total force (f_ji = -f_ij bitwise) is exactly zero.  r_s is
+    small here so that whole shell rows fit in one batch (p <= 64)."""
+    c = dict(N=N, rho=rho, jitter=0.3, rc=1.5, rs=2.2, skin=0.1, p=64, K=2, seed=seed)
+    x, v, L = _state(c)
+    lists = oracle.build_lists(x, L, c["rc"], c["rs"], c["skin"], K=2)
+    assert lists.n_shell.max() <= 64
+    a = _system(c, x, v, L, subtract_net_force=False).forces()
+    b = _system(c, x, v, L, full_list=True, subtract_net_force=False).forces()
+    assert np.array_equal(a, b)
+    q = np.rint(b * 2.0**24).astype(np.int64)
+    assert np.array_equal(q.astype(np.float64) / 2.0**24, b)
+    assert np.all(q.sum(0) == 0)
+    Fo, _ = oracle.full_forces(x, L, c["rs"], lists)
+    assert _relnorm(b, Fo) <= 1e-5
+
+
+def test_rdf_counts_exact(case):
+    c, x, v, L, lists = case
+    dr, nb = 0.02, int(c["rs"] / 0.02) - 1
+    for full in (False, True):
+        s = _system(c, x, v, L, full_list=full)
+        h = s.rdf(dr, nb)
+        assert np.array_equal(h, oracle.rdf_counts(x, L, dr, nb))
