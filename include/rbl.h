@@ -72,8 +72,9 @@ typedef struct {
     int full_list;        /* 1: classical cutoff with one full Verlet list (no batch) */
     int subtract_net_force; /* 1 (default): subtract the mean force (Appendix A) */
     int cells_per_cutoff; /* K: cell width >= (r_s + skin)/K, stencil (2K+1)^3; 1..3 */
-    int cap_core;         /* row capacities; 0 = derived from the density */
-    int cap_shell;        /* (shell row capacity, or full row capacity if full_list) */
+    int cap_core;         /* core row capacity; 0 = derived from the density */
+    int cap_stencil;      /* largest stencil population of a cell (shell/full rows are
+                             bitmasks over it); 0 = derived from the density */
 } rbl_params;
 
 typedef struct {

@@ -31,6 +31,7 @@ __global__ void k_zero(View v, int conditional)
         v.sc->ns_max = 0;
         v.sc->ns_sum = 0ull;
         v.sc->nc_sum = 0ull;
+        v.sc->m_max = 0;
     }
 }
 
@@ -224,81 +225,153 @@ __global__ void k_copy_back(View v, int conditional)
     v.ubuild[k] = p;
 }
 
-__device__ __forceinline__ int wrap_cell(int c, int n)
-{
-    c %= n;
-    return c < 0 ? c + n : c;
-}
+// K3: two-level lists (or the full list).  One warp per home cell: the warp walks
+// the cell's candidate sequence 32 candidates at a time (one per lane, fetched
+// once) and tests each against every particle of the cell:
+//   core : r2 <  (r_c + skin)^2                         -> explicit list (ballot rank)
+//   shell: max(r_c - skin, 0)^2 <= r2 < (r_s + skin)^2  -> mask word (ballot)
+//   full : r2 <  (r_s + skin)^2   (full_list mode, in the mask)
+// Candidates are visited in canonical order, so list order and bit order are the
+// canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
+// k.  Row lengths are counted past the core capacity.
+constexpr int kBuildWarps = 4;
+constexpr int kMaxSeg = kMaxStencil * kMaxStencil;
 
-// K3: two-level lists (or the full list).  One thread per particle walks the
-// stencil in canonical order (z-major, x-minor slots; members of a cell in tag
-// order) and appends every neighbour inside a window:
-//   core : r2 <  (r_c + skin)^2
-//   shell: max(r_c - skin, 0)^2 <= r2 < (r_s + skin)^2
-//   full : r2 <  (r_s + skin)^2          (full_list mode, stored in the shell rows)
-// Lengths are counted past the capacity so the caller learns the size needed.
-__global__ void __launch_bounds__(kBlock) k_build_lists(View v, int conditional)
+__global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int nc = 0, ns = 0;
-    if (i < v.N) {
-        int4 pi = v.pos[i];
-        int ci[3] = {cell_coord((unsigned)pi.x, v.n[0]), cell_coord((unsigned)pi.y, v.n[1]),
-                     cell_coord((unsigned)pi.z, v.n[2])};
-        int *crow = v.core + (size_t)i * v.cap_c;
-        int *srow = v.shell + (size_t)i * v.cap_s;
-        const bool full = v.full_list != 0;
-        for (int oz = 0; oz < v.nofs[2]; ++oz) {
-            int cz = wrap_cell(ci[2] + v.ofs[2][oz], v.n[2]);
-            for (int oy = 0; oy < v.nofs[1]; ++oy) {
-                int cy = wrap_cell(ci[1] + v.ofs[1][oy], v.n[1]);
-                int rowbase = (cz * v.n[1] + cy) * v.n[0];
-                for (int ox = 0; ox < v.nofs[0]; ++ox) {
-                    int c = rowbase + wrap_cell(ci[0] + v.ofs[0][ox], v.n[0]);
-                    int s = v.start[c], e = v.start[c + 1];
-                    for (int j = s; j < e; ++j) {
-                        if (j == i) continue;
-                        PairGeom g = pair_geom(pi, v.pos[j], v.h);
-                        if (full) {
-                            if (g.r2 < v.t_cut_list) {
-                                if (ns < v.cap_s) srow[ns] = j;
-                                ++ns;
-                            }
-                        } else {
-                            if (g.r2 < v.t_core_list) {
-                                if (nc < v.cap_c) crow[nc] = j;
-                                ++nc;
-                            }
-                            if (g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list) {
-                                if (ns < v.cap_s) srow[ns] = j;
-                                ++ns;
-                            }
-                        }
+    __shared__ int s_pre[kBuildWarps][kMaxSeg + 1];
+    __shared__ int s_a[kBuildWarps][kMaxSeg], s_la[kBuildWarps][kMaxSeg], s_b[kBuildWarps][kMaxSeg];
+    __shared__ int4 s_pos[kBuildWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kBuildWarps + warp;
+    if (c >= v.ncell) return; // whole warp; no block-wide barrier below
+    int *pre = s_pre[warp], *sA = s_a[warp], *lA = s_la[warp], *sB = s_b[warp];
+    const int cx = c % v.n[0], cy = (c / v.n[0]) % v.n[1], cz = c / (v.n[0] * v.n[1]);
+    const int S = v.S;
+    for (int sg = lane; sg < S; sg += 32) {
+        int oz = sg / v.nofs[1], oy = sg - oz * v.nofs[1];
+        int czz = wrap_cell(cz + v.ofs[2][oz], v.n[2]);
+        int cyy = wrap_cell(cy + v.ofs[1][oy], v.n[1]);
+        int rowbase = (czz * v.n[1] + cyy) * v.n[0];
+        int fx = wrap_cell(cx + v.ofs[0][0], v.n[0]);
+        int last = fx + v.nofs[0] - 1;
+        int lastA = last < v.n[0] ? last : v.n[0] - 1;
+        int a0 = v.start[rowbase + fx];
+        int la = v.start[rowbase + lastA + 1] - a0;
+        int b0 = v.start[rowbase];
+        int lb = last >= v.n[0] ? v.start[rowbase + (last - v.n[0]) + 1] - b0 : 0;
+        sA[sg] = a0;
+        lA[sg] = la;
+        sB[sg] = b0;
+        pre[sg + 1] = la + lb;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        pre[0] = 0;
+        for (int sg = 1; sg <= S; ++sg) pre[sg] += pre[sg - 1];
+    }
+    __syncwarp();
+    int *gp = v.seg_prefix + (size_t)c * (S + 1);
+    for (int sg = lane; sg <= S; sg += 32) gp[sg] = pre[sg];
+    const int s0 = v.start[c], s1 = v.start[c + 1];
+    const int M = pre[S];
+    if (s1 == s0) return;
+    // the masks index this cell's candidate sequence: remember the cell until the
+    // next build, however far the particle drifts meanwhile
+    for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = pack_cell(cx, cy, cz);
+    if (M > v.Mcap) {
+        // too many candidates for the masks: flag it and leave these particles with
+        // empty rows so that no kernel decodes a mask that was not written
+        for (int i = s0 + lane; i < s1; i += 32) {
+            v.n_core[i] = 0;
+            v.n_shell[i] = 0;
+        }
+        if (lane == 0) {
+            atomicOr(&v.sc->flags, kFlagCellOverflow);
+            atomicMax(&v.sc->m_max, M);
+        }
+        return;
+    }
+    const int nchunk = (M + 31) >> 5;
+    const bool full = v.full_list != 0;
+    const size_t N = (size_t)v.N;
+    const unsigned lt = (1u << lane) - 1u;
+    int wmc = 0, wms = 0;
+    unsigned long long wsc = 0ull, wss = 0ull;
+    for (int base = s0; base < s1; base += 32) {
+        const int mm = min(32, s1 - base);
+        if (lane < mm) s_pos[warp][lane] = v.pos[base + lane];
+        __syncwarp();
+        int my_nc = 0, my_ns = 0; // counters of particle base + lane
+        int seg = 0;
+        for (int k = 0; k < nchunk; ++k) {
+            const int cand = (k << 5) + lane;
+            const bool valid = cand < M;
+            int sg = seg;
+            while (sg + 1 < S && pre[sg + 1] <= cand) ++sg;
+            const int off = cand - pre[sg];
+            const int j = off < lA[sg] ? sA[sg] + off : sB[sg] + (off - lA[sg]);
+            const int4 pj = valid ? v.pos[j] : make_int4(0, 0, 0, 0);
+            seg = __shfl_sync(0xffffffffu, sg, 31);
+            for (int q = 0; q < mm; ++q) {
+                const int i = base + q;
+                PairGeom g = pair_geom(s_pos[warp][q], pj, v.h);
+                const bool other = valid && j != i;
+                bool in_core, in_shell;
+                if (full) {
+                    in_core = false;
+                    in_shell = other && g.r2 < v.t_cut_list;
+                } else {
+                    in_core = other && g.r2 < v.t_core_list;
+                    in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
+                }
+                const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
+                if (lane == 0) v.mask[(size_t)k * N + i] = bs;
+                if (lane == q) my_ns += __popc(bs);
+                const unsigned bc = __ballot_sync(0xffffffffu, in_core);
+                if (bc) {
+                    const int nc_q = __shfl_sync(0xffffffffu, my_nc, q);
+                    if (in_core) {
+                        int r = nc_q + __popc(bc & lt);
+                        if (r < v.cap_c) v.core[(size_t)r * N + i] = j;
                     }
+                    if (lane == q) my_nc += __popc(bc);
                 }
             }
         }
-        v.n_core[i] = nc;
-        v.n_shell[i] = ns;
-        if (nc > v.cap_c || ns > v.cap_s) atomicOr(&v.sc->flags, kFlagOverflow);
+        if (lane < mm) {
+            v.n_core[base + lane] = my_nc;
+            v.n_shell[base + lane] = my_ns;
+            if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
+            wmc = max(wmc, my_nc);
+            wms = max(wms, my_ns);
+            wsc += (unsigned long long)my_nc;
+            wss += (unsigned long long)my_ns;
+        }
+        __syncwarp();
     }
-    // row statistics
-    int mc = nc, ms = ns;
-    unsigned long long ss = (unsigned long long)ns, cs = (unsigned long long)nc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-        ms = max(ms, __shfl_xor_sync(0xffffffffu, ms, o));
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        wmc = max(wmc, __shfl_xor_sync(0xffffffffu, wmc, o));
+        wms = max(wms, __shfl_xor_sync(0xffffffffu, wms, o));
+        wsc += __shfl_xor_sync(0xffffffffu, wsc, o);
+        wss += __shfl_xor_sync(0xffffffffu, wss, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&v.sc->nc_max, mc);
-        atomicMax(&v.sc->ns_max, ms);
-        atomicAdd(&v.sc->ns_sum, ss);
-        atomicAdd(&v.sc->nc_sum, cs);
+    if (lane == 0) {
+        atomicMax(&v.sc->nc_max, wmc);
+        atomicMax(&v.sc->ns_max, wms);
+        atomicMax(&v.sc->m_max, M);
+        atomicAdd(&v.sc->nc_sum, wsc);
+        atomicAdd(&v.sc->ns_sum, wss);
     }
+}
+
+// Graph form of the rebuild decision: set the conditional node's value from the
+// device flag the integrator raised.
+__global__ void k_set_condition(View v, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, v.sc->rebuild ? 1u : 0u);
 }
 
 __global__ void k_finish(View v, int conditional)
@@ -325,8 +398,14 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_sort_cells<<<gC, kBlock, 0, s>>>(v, cond);
     k_permute<<<gN, kBlock, 0, s>>>(v, cond);
     k_copy_back<<<gN, kBlock, 0, s>>>(v, cond);
-    k_build_lists<<<gN, kBlock, 0, s>>>(v, cond);
+    k_build_lists<<<ceil_div(v.ncell, kBuildWarps), kBuildWarps * 32, 0, s>>>(v, cond);
     k_finish<<<1, 1, 0, s>>>(v, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    k_set_condition<<<1, 1, 0, s>>>(v, h);
     return cudaGetLastError();
 }
 

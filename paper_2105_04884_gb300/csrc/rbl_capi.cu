@@ -24,7 +24,7 @@ struct Layout {
     size_t off[32];
     int n;
     size_t total;
-    int cap_c, cap_s, ncell, n3[3], ntiles, nblk;
+    int cap_c, W, S, Mcap, ncell, n3[3], nofs3[3], ntiles, nblk;
     size_t staging_bytes;
 };
 
@@ -63,7 +63,10 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
     for (int a = 0; a < 3; ++a)
         if (!(p->L[a] >= 2.0 * (p->r_s + p->skin)))
             BAD("box length L[%d]=%g is below 2 (r_s + skin) = %g", a, p->L[a], 2.0 * (p->r_s + p->skin));
-    if (p->cap_core < 0 || p->cap_shell < 0) BAD("capacities must be >= 0");
+    if (p->cap_core < 0 || p->cap_stencil < 0) BAD("capacities must be >= 0");
+    for (int a = 0; a < 3; ++a)
+        if (std::floor(p->L[a] * p->cells_per_cutoff / (p->r_s + p->skin)) > (double)(1 << kCellBits))
+            BAD("box too large: more than %d cells along axis %d", 1 << kCellBits, a);
     return RBL_OK;
 #undef BAD
 }
@@ -74,22 +77,25 @@ Layout make_layout(const rbl_params *p, int N)
     double V = p->L[0] * p->L[1] * p->L[2];
     double rho = N / V;
     double rcut = p->r_s + p->skin;
-    double lo = p->r_c - p->skin > 0.0 ? p->r_c - p->skin : 0.0;
     double core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
-    double shell_mean = rho * 4.0 / 3.0 * kPi * (std::pow(rcut, 3) - std::pow(lo, 3));
-    double full_mean = rho * 4.0 / 3.0 * kPi * std::pow(rcut, 3);
-    auto cap_of = [&](double mean) { return round_up((int)std::ceil(1.6 * mean + 24.0), 8); };
-    L.cap_c = p->full_list ? 8 : (p->cap_core > 0 ? round_up(p->cap_core, 4) : cap_of(core_mean));
-    L.cap_s = p->cap_shell > 0 ? round_up(p->cap_shell, 4) : cap_of(p->full_list ? full_mean : shell_mean);
+    L.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
     int K = p->cells_per_cutoff;
     long long nc = 1;
+    double span = 1.0;
     for (int a = 0; a < 3; ++a) {
         int n = (int)std::floor(p->L[a] * (double)K / rcut);
         if (n < 1) n = 1;
         L.n3[a] = n;
+        L.nofs3[a] = n >= 2 * K + 1 ? 2 * K + 1 : n;
+        span *= L.nofs3[a] * (p->L[a] / n);
         nc *= n;
     }
     L.ncell = (int)nc;
+    L.S = L.nofs3[1] * L.nofs3[2];
+    int mcap = p->cap_stencil > 0 ? p->cap_stencil : (int)std::ceil(1.3 * rho * span + 96.0);
+    if (mcap > N) mcap = N;
+    L.Mcap = round_up(mcap, 32);
+    L.W = L.Mcap / 32;
     L.ntiles = (L.ncell + 2047) / 2048;
     L.nblk = (N + kBlock - 1) / kBlock;
     size_t Nz = (size_t)N;
@@ -106,9 +112,11 @@ Layout make_layout(const rbl_params *p, int N)
         4 * Nz, 4 * Nz,                             // cell, order
         4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), // counts, start, fill
         4 * ((size_t)L.ntiles + 1),                 // blocksums
+        4 * (size_t)L.ncell * (size_t)(L.S + 1),    // seg_prefix
         4 * Nz * (size_t)L.cap_c, 4 * Nz,           // core, n_core
-        4 * Nz * (size_t)L.cap_s, 4 * Nz,           // shell, n_shell
-        64 * (size_t)L.nblk,                        // partials [nblk][8] doubles
+        4 * Nz * (size_t)L.W, 4 * Nz,               // mask, n_shell
+        4 * Nz,                                     // hcell
+        64 * (size_t)((N + kMinBlock - 1) / kMinBlock), // partials [blocks][8] doubles, any block size >= kMinBlock
         sizeof(DevScalars),                         // scalars
         L.staging_bytes,                            // staging
     };
@@ -144,8 +152,8 @@ rbl_status check_flags(rbl_ctx *ctx)
     if (st != RBL_OK) return st;
     unsigned f = ctx->h_sc->flags;
     if (f & (kFlagOverflow | kFlagCellOverflow)) {
-        set_err(ctx, "list row or cell over capacity (longest core row %d / cap %d, longest shell row %d / cap %d)",
-                ctx->h_sc->nc_max, ctx->view.cap_c, ctx->h_sc->ns_max, ctx->view.cap_s);
+        set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest stencil population %d / cap %d)",
+                ctx->h_sc->nc_max, ctx->view.cap_c, ctx->h_sc->m_max, ctx->view.Mcap);
         return RBL_EOVERFLOW;
     }
     if (f & kFlagNonFinite) {
@@ -210,24 +218,58 @@ rbl_status ensure_events(rbl_ctx *ctx, int steps)
     return RBL_OK;
 }
 
+// Steady-state step as a CUDA graph: kick/drift/thermostat, a kernel that copies the
+// device rebuild flag into a conditional handle, an IF node whose body is the whole
+// rebuild chain, then the force and its reduction.  No host round trip and no
+// empty launches when no rebuild is due.
 rbl_status ensure_graph(rbl_ctx *ctx)
 {
     if (ctx->graph_exec) return RBL_OK;
-    cudaGraph_t g = nullptr;
+    cudaStream_t s = ctx->stream;
     cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
-    CK(cudaStreamBeginCapture(ctx->stream, mode));
-    cudaError_t e = enqueue_step(ctx, ctx->prm.dt, false);
-    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        set_err(ctx, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-        return RBL_ECUDA;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, g, 0, cudaGraphCondAssignDefault);
+    cudaGraphNode_t cond_node = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, mode);
+    if (e == cudaSuccess) {
+        cudaError_t ec = launch_integrate(ctx->view, ctx->prm.dt, true, s);
+        if (ec == cudaSuccess) ec = launch_set_rebuild_condition(ctx->view, handle, s);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        if (ec == cudaSuccess) ec = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (ec == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            ec = cudaGraphAddNode(&cond_node, g, deps, nullptr, ndeps, &cp);
+        }
+        if (ec == cudaSuccess) ec = cudaStreamUpdateCaptureDependencies(s, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (ec == cudaSuccess) ec = launch_forces(ctx->view, 1, 1, false, s);
+        cudaGraph_t gout = nullptr;
+        e = cudaStreamEndCapture(s, &gout);
+        if (ec != cudaSuccess) e = ec;
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, mode);
+        if (e == cudaSuccess) {
+            cudaError_t ec = launch_rebuild(ctx->view, ctx->n_scan_blocks, false, s);
+            cudaGraph_t bout = nullptr;
+            e = cudaStreamEndCapture(s, &bout);
+            if (ec != cudaSuccess) e = ec;
+        }
     }
     cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        set_err(ctx, "graph instantiate failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        set_err(ctx, "building the step graph failed: %s", cudaGetErrorString(e));
         return RBL_ECUDA;
     }
     ctx->graph_exec = ex;
@@ -292,7 +334,9 @@ rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t work
     v.p = prm->p;
     v.K = prm->cells_per_cutoff;
     v.cap_c = L.cap_c;
-    v.cap_s = L.cap_s;
+    v.W = L.W;
+    v.S = L.S;
+    v.Mcap = L.Mcap;
     v.full_list = prm->full_list ? 1 : 0;
     v.precision = prm->precision;
     v.subtract = prm->subtract_net_force ? 1 : 0;
@@ -300,13 +344,8 @@ rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t work
     for (int a = 0; a < 3; ++a) {
         int n = L.n3[a], K = prm->cells_per_cutoff;
         v.n[a] = n;
-        if (n >= 2 * K + 1) {
-            v.nofs[a] = 2 * K + 1;
-            for (int o = 0; o < 2 * K + 1; ++o) v.ofs[a][o] = o - K;
-        } else {
-            v.nofs[a] = n;
-            for (int o = 0; o < n; ++o) v.ofs[a][o] = o;
-        }
+        v.nofs[a] = L.nofs3[a];
+        for (int o = 0; o < L.nofs3[a]; ++o) v.ofs[a][o] = n >= 2 * K + 1 ? o - K : o;
         v.L[a] = prm->L[a];
         v.inv[a] = 4294967296.0 / prm->L[a];
         v.h[a] = (float)(prm->L[a] / 4294967296.0);
@@ -342,17 +381,19 @@ rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t work
     v.start = (int *)(base + L.off[k++]);
     v.fill = (int *)(base + L.off[k++]);
     v.blocksums = (int *)(base + L.off[k++]);
+    v.seg_prefix = (int *)(base + L.off[k++]);
     v.core = (int *)(base + L.off[k++]);
     v.n_core = (int *)(base + L.off[k++]);
-    v.shell = (int *)(base + L.off[k++]);
+    v.mask = (unsigned *)(base + L.off[k++]);
     v.n_shell = (int *)(base + L.off[k++]);
+    v.hcell = (int *)(base + L.off[k++]);
     v.partials = (double *)(base + L.off[k++]);
     v.sc = (DevScalars *)(base + L.off[k++]);
     v.staging = (double *)(base + L.off[k++]);
     ctx->staging_bytes = L.staging_bytes;
     cudaError_t e = cudaMemsetAsync(v.sc, 0, sizeof(DevScalars), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)N, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * (size_t)L.nblk, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * (size_t)((N + kMinBlock - 1) / kMinBlock), ctx->stream);
     if (e != cudaSuccess) {
         set_err(ctx, "initialisation failed: %s", cudaGetErrorString(e));
         *out = ctx;
@@ -525,20 +566,47 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
     if (st != RBL_OK) return st;
     const View &v = ctx->view;
     size_t N = (size_t)v.N;
-    int rcap = kind == 0 ? v.cap_c : v.cap_s;
-    std::vector<int> tag(N), cnt(N), data(N * (size_t)rcap);
+    std::vector<int> tag(N), cnt(N);
     CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(cnt.data(), kind == 0 ? v.n_core : v.n_shell, 4 * N, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(data.data(), kind == 0 ? v.core : v.shell, 4 * N * (size_t)rcap, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < N; ++i) {
-        int t = tag[i];
-        int n = cnt[i];
-        if (n > cap) {
-            set_err(ctx, "row of tag %d has %d entries, more than cap %d", t, n, cap);
+    for (size_t i = 0; i < N; ++i)
+        if (cnt[i] > cap) {
+            set_err(ctx, "row of tag %d has %d entries, more than cap %d", tag[i], cnt[i], cap);
             return RBL_EOVERFLOW;
         }
-        counts[t] = n;
-        for (int k = 0; k < n; ++k) rows[(size_t)t * cap + k] = tag[data[i * rcap + k]];
+    if (kind == 0) {
+        std::vector<int> core(N * (size_t)v.cap_c);
+        CK(cudaMemcpy(core.data(), v.core, core.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < N; ++i) {
+            int t = tag[i];
+            counts[t] = cnt[i];
+            for (int k = 0; k < cnt[i]; ++k) rows[(size_t)t * cap + k] = tag[core[(size_t)k * N + i]];
+        }
+        return RBL_OK;
+    }
+    // decode the masks on the host with the same segment walk as the kernels
+    std::vector<unsigned> mask(N * (size_t)v.W);
+    std::vector<int> start((size_t)v.ncell + 1), prefix((size_t)v.ncell * (v.S + 1));
+    std::vector<int> hcell(N);
+    CK(cudaMemcpy(mask.data(), v.mask, mask.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(start.data(), v.start, start.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(prefix.data(), v.seg_prefix, prefix.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hcell.data(), v.hcell, 4 * N, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) {
+        int t = tag[i];
+        counts[t] = cnt[i];
+        int c = cell_index(v, hcell[i]);
+        SegCursor cur;
+        cur.init(v, start.data(), prefix.data() + (size_t)c * (v.S + 1), hcell[i]);
+        int k = 0;
+        for (int w = 0; w < v.W && k < cnt[i]; ++w) {
+            unsigned word = mask[(size_t)w * N + i];
+            while (word) {
+                int bit = __builtin_ctz(word);
+                word &= word - 1u;
+                rows[(size_t)t * cap + k++] = tag[cur.index_of(v, (w << 5) + bit)];
+            }
+        }
     }
     return RBL_OK;
 }
@@ -550,33 +618,19 @@ rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
     if (st != RBL_OK) return st;
     const View &v = ctx->view;
     size_t N = (size_t)v.N;
-    int *dpos = (int *)v.staging;
-    int *dn = dpos + N * (size_t)v.p;
-    CK(launch_batch(v, (unsigned long long)step, dpos, dn, ctx->stream));
+    int *dj = (int *)v.staging;
+    int *dn = dj + N * (size_t)v.p;
+    CK(launch_batch(v, (unsigned long long)step, dj, dn, ctx->stream));
     st = check_flags(ctx);
     if (st != RBL_OK) return st;
-    std::vector<int> tag(N), pos(N * (size_t)v.p), nb(N), ns(N), shell;
+    std::vector<int> tag(N), jj(N * (size_t)v.p), nb(N);
     CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(pos.data(), dpos, 4 * N * (size_t)v.p, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(jj.data(), dj, 4 * N * (size_t)v.p, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(nb.data(), dn, 4 * N, cudaMemcpyDeviceToHost));
-    shell.resize(N * (size_t)v.cap_s);
-    CK(cudaMemcpy(shell.data(), v.shell, 4 * N * (size_t)v.cap_s, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < N; ++i) {
         int t = tag[i];
-        int m = nb[i];
-        int *dst = batch + (size_t)t * v.p;
-        for (int q = 0; q < m; ++q) dst[q] = pos[i * v.p + q];
-        // ascending row position, then translate to neighbour tags
-        for (int a = 1; a < m; ++a) {
-            int x = dst[a], b = a - 1;
-            while (b >= 0 && dst[b] > x) {
-                dst[b + 1] = dst[b];
-                --b;
-            }
-            dst[b + 1] = x;
-        }
-        for (int q = 0; q < m; ++q) dst[q] = tag[shell[i * v.cap_s + dst[q]]];
-        counts[t] = m;
+        counts[t] = nb[i];
+        for (int q = 0; q < nb[i]; ++q) batch[(size_t)t * v.p + q] = tag[jj[i * v.p + q]];
     }
     return RBL_OK;
 }

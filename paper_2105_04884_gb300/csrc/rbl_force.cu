@@ -2,49 +2,23 @@
 // force, and the parity/observable kernels that share their pair rule.
 //
 // One thread per particle (cell order).  Core row: every entry with r < r_c is
-// summed.  Shell row: a Floyd p-subset of positions is drawn from Philox stream 0 of
-// (seed, step, tag) -- or the whole row when N_s <= p -- and every drawn entry with
-// r_c <= r < r_s contributes s f_ij, s = N_s / p.
+// summed.  Shell row: a Floyd p-subset of row positions is drawn from Philox stream
+// 0 of (seed, step, tag) -- or the whole row when N_s <= p -- sorted, and located in
+// the shell mask by counting set bits; every drawn entry with r_c <= r < r_s
+// contributes s f_ij, s = N_s / p.  The mask words are read column-major, so a warp
+// reads 32 consecutive particles' words in one transaction, and the walk stops at
+// the word holding the last drawn position.
 //
 // FP32 path: pair arithmetic in binary32, each pair's force (times s) converted
 // exactly to fixed point at scale 2^24 and summed in integers, so the sum does not
-// depend on the order or on the thread mapping; the total force is accumulated
-// with 64-bit integer atomics (exact).  FP64 path: FP64 pair arithmetic from the
-// FP64 positions, per-block partial sums reduced in a fixed order.
+// depend on order or thread mapping; the total force is accumulated with 64-bit
+// integer atomics (exact).  FP64 path: FP64 pair arithmetic from the FP64 positions,
+// per-block partial sums reduced in a fixed order.
 #include "rbl_internal.cuh"
 
 namespace rbl {
 
 namespace {
-
-struct Pair64 {
-    double f[3];
-    double u, w;
-};
-
-// FP64 pair force from FP64 positions (minimum image by rounding d/L).
-__device__ __forceinline__ void pair64(const View &v, int i, int j, Pair64 &out)
-{
-    size_t N = (size_t)v.N;
-    double r2 = 0.0;
-    double d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double t = v.x[a * N + i] - v.x[a * N + j];
-        t -= v.L[a] * rint(t / v.L[a]);
-        d[a] = t;
-    }
-    r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    double inv = 1.0 / r2;
-    double r6 = inv * inv * inv;
-    double vir = 24.0 * (2.0 * r6 * r6 - r6);
-    double coef = vir * inv;
-    out.f[0] = coef * d[0];
-    out.f[1] = coef * d[1];
-    out.f[2] = coef * d[2];
-    out.u = 4.0 * (r6 * r6 - r6);
-    out.w = vir;
-}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x)
@@ -55,10 +29,10 @@ __device__ __forceinline__ T warp_sum(T x)
 }
 
 // Deterministic block sum (fixed tree) of NV doubles per thread into out[0..NV).
-template <int NV>
+template <int NV, int BLOCK>
 __device__ __forceinline__ void block_sum_d(double (&x)[NV], double *out)
 {
-    __shared__ double sh[NV][kBlock / 32];
+    __shared__ double sh[NV][BLOCK / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -68,113 +42,284 @@ __device__ __forceinline__ void block_sum_d(double (&x)[NV], double *out)
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
+        for (int w = 0; w < BLOCK / 32; ++w) s += sh[threadIdx.x][w];
         out[threadIdx.x] = s;
     }
 }
 
-// MODE 0: RBL (core + sampled shell); MODE 1: full list (rows in the shell arrays).
-template <int MODE, bool FP32, bool ENERGY>
-__global__ void __launch_bounds__(kBlock) k_force(View v, int step_offset)
+// Per-particle accumulators.  FP32 path: binary32 pair terms summed in binary32 in
+// the canonical order (core row order, then the batch in ascending row position),
+// the shell sum scaled by s once; the per-particle total is converted exactly to
+// int64 fixed point (scale 2^24) for every cross-particle sum.  FP64 path: FP64
+// pair terms from the FP64 positions.
+template <bool FP32, bool ENERGY>
+struct Accum {
+    float f32[2][3], e32[2], w32[2];   // [0] core, [1] shell (before the batch scale)
+    double f64[2][3], e64[2], w64[2];
+
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                f32[r][a] = 0.f;
+                f64[r][a] = 0.0;
+            }
+            e32[r] = w32[r] = 0.f;
+            e64[r] = w64[r] = 0.0;
+        }
+    }
+
+    __device__ __forceinline__ static bool in_region(const View &v, float r2, int part)
+    {
+        if (v.full_list) return r2 < v.t_rs2;
+        return part == 0 ? r2 < v.t_rc2 : (r2 >= v.t_rc2 && r2 < v.t_rs2);
+    }
+
+    // Pair (i, j) in region `part` (0 core, 1 shell / full).
+    __device__ __forceinline__ void pair(const View &v, int4 pi, int4 pj, int i, int j, int part)
+    {
+        PairGeom g = pair_geom(pi, pj, v.h);
+        bool inside = in_region(v, g.r2, part);
+        if (FP32) {
+            float u, w;
+            float coef = lj_coef(g.r2, &u, &w);
+            coef = inside ? coef : 0.f;
+            f32[part][0] = __fmaf_rn(coef, g.dx, f32[part][0]);
+            f32[part][1] = __fmaf_rn(coef, g.dy, f32[part][1]);
+            f32[part][2] = __fmaf_rn(coef, g.dz, f32[part][2]);
+            if (ENERGY && inside) {
+                e32[part] += u;
+                w32[part] += w;
+            }
+        } else if (inside) {
+            size_t N = (size_t)v.N;
+            double d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double t = v.x[a * N + i] - v.x[a * N + j];
+                t -= v.L[a] * rint(t / v.L[a]);
+                d[a] = t;
+            }
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double inv = 1.0 / r2;
+            double r6 = inv * inv * inv;
+            double vir = 24.0 * (2.0 * r6 * r6 - r6);
+            double coef = vir * inv;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f64[part][a] += coef * d[a];
+            e64[part] += 4.0 * (r6 * r6 - r6);
+            w64[part] += vir;
+        }
+    }
+
+    // kGather pairs: indices jj[u] (valid for u < cnt), gathered before any is used.
+    template <int G>
+    __device__ __forceinline__ void pairs(const View &v, int4 pi, int i, const int (&jj)[G], int cnt, int part)
+    {
+        int4 pj[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) pj[u] = v.pos[u < cnt ? jj[u] : i];
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+            if (u < cnt) pair(v, pi, pj[u], i, jj[u], part);
+    }
+};
+
+__device__ __forceinline__ void sort_small(int *S, int n)
 {
+    for (int a = 1; a < n; ++a) {
+        int x = S[a], b = a - 1;
+        while (b >= 0 && S[b] > x) {
+            S[b + 1] = S[b];
+            --b;
+        }
+        S[b + 1] = x;
+    }
+}
+
+// MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (mask).
+// PMAX > 0: batch positions and neighbour indices live in registers (p <= PMAX);
+// PMAX = 0: general path through local arrays (p up to kMaxP).
+//
+// Memory-level parallelism: the core indices and the mask words of a thread are
+// staged in shared memory with bursts of independent loads (column-major storage
+// makes every burst coalesced across the warp), the batch is drawn while those
+// loads are in flight, and neighbour positions are gathered kGather at a time
+// before their pair terms are computed.
+constexpr int kForceThreads = 128;
+static_assert(kForceThreads >= kMinBlock, "per-block partials are sized for kMinBlock");
+constexpr int kCoreStage = 32;  // core entries staged per thread (longer rows read directly)
+constexpr int kMaskStage = 40;  // mask words staged per thread
+constexpr int kGather = 8;
+
+template <int MODE, bool FP32, bool ENERGY, int PMAX>
+__global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset)
+{
+    __shared__ int s_core[MODE == 0 ? kCoreStage : 1][kForceThreads];
+    __shared__ unsigned s_mask[kMaskStage][kForceThreads];
     const unsigned long long step = v.sc->step + (unsigned long long)step_offset;
-    int i = blockIdx.x * kBlock + threadIdx.x;
-    bool active = i < v.N;
-    long long q[3] = {0, 0, 0};
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * kForceThreads + t;
+    const size_t N = (size_t)v.N;
+    long long qv[3] = {0, 0, 0};
     double f64[3] = {0.0, 0.0, 0.0};
     double e_i = 0.0, w_i = 0.0;
-    if (active) {
-        int4 pi = v.pos[i];
-        FixedAcc acc;
-        acc.zero();
-        float e_c = 0.f, w_c = 0.f, e_s = 0.f, w_s = 0.f;
-        double e_c64 = 0.0, w_c64 = 0.0, e_s64 = 0.0, w_s64 = 0.0;
-        double fc[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
-        if (MODE == 0) {
-            int nc = min(v.n_core[i], v.cap_c);
-            const int *crow = v.core + (size_t)i * v.cap_c;
-            for (int k = 0; k < nc; ++k) {
-                int j = crow[k];
-                PairGeom g = pair_geom(pi, v.pos[j], v.h);
-                bool in = g.r2 < v.t_rc2;
-                if (FP32) {
-                    float u, w;
-                    float coef = lj_coef(g.r2, &u, &w);
-                    coef = in ? coef : 0.f;
-                    acc.add(__fmul_rn(coef, g.dx), __fmul_rn(coef, g.dy), __fmul_rn(coef, g.dz));
-                    if (ENERGY && in) {
-                        e_c += u;
-                        w_c += w;
-                    }
-                } else if (in) {
-                    Pair64 pr;
-                    pair64(v, i, j, pr);
+    if (i < v.N) {
+        const int4 pi = v.pos[i];
+        const int nc = MODE == 0 ? min(v.n_core[i], v.cap_c) : 0;
+        const int ns = v.n_shell[i];
+        const int hc = v.hcell[i];
+        const int *prefix = v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1);
+        const int nwords = min((prefix[v.S] + 31) >> 5, v.W);
+        // stage core indices and mask words (independent loads, in bursts)
+        const int ncs = min(nc, kCoreStage);
+        for (int k0 = 0; k0 < ncs; k0 += 8) {
+            int tmp[8];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) fc[a] += pr.f[a];
-                    e_c64 += pr.u;
-                    w_c64 += pr.w;
-                }
-            }
+            for (int u = 0; u < 8; ++u) tmp[u] = k0 + u < ncs ? v.core[(size_t)(k0 + u) * N + i] : 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k0 + u < ncs) s_core[k0 + u][t] = tmp[u];
         }
-        int ns = min(v.n_shell[i], v.cap_s);
-        const int *srow = v.shell + (size_t)i * v.cap_s;
-        int S[kMaxP];
-        int nb;
+        const int nws = min(nwords, kMaskStage);
+        for (int w0 = 0; w0 < nws; w0 += 8) {
+            unsigned tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tmp[u] = w0 + u < nws ? v.mask[(size_t)(w0 + u) * N + i] : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (w0 + u < nws) s_mask[w0 + u][t] = tmp[u];
+        }
+        auto mask_word = [&](int w) -> unsigned {
+            return w < kMaskStage ? s_mask[w][t] : v.mask[(size_t)w * N + i];
+        };
+        Accum<FP32, ENERGY> acc;
+        acc.zero();
+        SegCursor cur;
+        cur.init(v, v.start, prefix, hc);
         float s32 = 1.0f;
         double s64 = 1.0;
         if (MODE == 0) {
-            nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
-            if (ns > v.p) {
-                s32 = __fdiv_rn((float)ns, (float)v.p);
-                s64 = (double)ns / (double)v.p;
+            // shell batch: positions in the row -> particle indices
+            if constexpr (PMAX > 0) {
+                int S[PMAX];
+                const int nb = batch_sorted<PMAX>(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                if (ns > v.p) {
+                    s32 = __fdiv_rn((float)ns, (float)v.p);
+                    s64 = (double)ns / (double)v.p;
+                }
+                int J[PMAX];
+                int w = 0, seen = 0;
+                unsigned word = nb > 0 ? mask_word(0) : 0u;
+                int cnt = __popc(word);
+#pragma unroll
+                for (int q = 0; q < PMAX; ++q) {
+                    J[q] = i;
+                    if (q < nb) {
+                        const int tq = S[q];
+                        while (tq >= seen + cnt) {
+                            seen += cnt;
+                            word = mask_word(++w);
+                            cnt = __popc(word);
+                        }
+                        J[q] = cur.index_of(v, (w << 5) + select_bit(word, tq - seen));
+                    }
+                }
+#pragma unroll
+                for (int q0 = 0; q0 < PMAX; q0 += kGather) {
+                    if (q0 < nb) {
+                        int jj[kGather];
+#pragma unroll
+                        for (int u = 0; u < kGather; ++u) jj[u] = J[q0 + u];
+                        acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
+                    }
+                }
+            } else {
+                int S[kMaxP];
+                const int nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                if (ns > v.p) {
+                    s32 = __fdiv_rn((float)ns, (float)v.p);
+                    s64 = (double)ns / (double)v.p;
+                    sort_small(S, nb);
+                }
+                int w = 0, seen = 0;
+                unsigned word = nb > 0 ? mask_word(0) : 0u;
+                int cnt = __popc(word);
+                for (int q0 = 0; q0 < nb; q0 += kGather) {
+                    int jj[kGather];
+#pragma unroll
+                    for (int u = 0; u < kGather; ++u) {
+                        jj[u] = i;
+                        if (q0 + u < nb) {
+                            const int tq = S[q0 + u];
+                            while (tq >= seen + cnt) {
+                                seen += cnt;
+                                word = mask_word(++w);
+                                cnt = __popc(word);
+                            }
+                            jj[u] = cur.index_of(v, (w << 5) + select_bit(word, tq - seen));
+                        }
+                    }
+                    acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
+                }
+            }
+            // core row, kGather at a time
+            for (int k0 = 0; k0 < nc; k0 += kGather) {
+                int jj[kGather];
+#pragma unroll
+                for (int u = 0; u < kGather; ++u) {
+                    const int k = k0 + u;
+                    jj[u] = k < nc ? (k < kCoreStage ? s_core[k][t] : v.core[(size_t)k * N + i]) : i;
+                }
+                acc.template pairs<kGather>(v, pi, i, jj, nc - k0, 0);
             }
         } else {
-            nb = ns;
-        }
-        for (int q_ = 0; q_ < nb; ++q_) {
-            int j = srow[MODE == 0 ? S[q_] : q_];
-            PairGeom g = pair_geom(pi, v.pos[j], v.h);
-            bool in = MODE == 0 ? (g.r2 >= v.t_rc2 && g.r2 < v.t_rs2) : (g.r2 < v.t_rs2);
-            if (FP32) {
-                float u, w;
-                float coef = lj_coef(g.r2, &u, &w);
-                coef = in ? coef : 0.f;
-                acc.add(__fmul_rn(__fmul_rn(coef, g.dx), s32), __fmul_rn(__fmul_rn(coef, g.dy), s32),
-                        __fmul_rn(__fmul_rn(coef, g.dz), s32));
-                if (ENERGY && in) {
-                    e_s += u;
-                    w_s += w;
-                }
-            } else if (in) {
-                Pair64 pr;
-                pair64(v, i, j, pr);
+            // full list: walk the mask, kGather members at a time
+            int w = 0;
+            unsigned word = ns > 0 ? mask_word(0) : 0u;
+            for (int k0 = 0; k0 < ns; k0 += kGather) {
+                int jj[kGather];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) fs[a] += pr.f[a];
-                e_s64 += pr.u;
-                w_s64 += pr.w;
+                for (int u = 0; u < kGather; ++u) {
+                    jj[u] = i;
+                    if (k0 + u < ns) {
+                        while (word == 0u) word = mask_word(++w);
+                        const int bit = __ffs(word) - 1;
+                        word &= word - 1u;
+                        jj[u] = cur.index_of(v, (w << 5) + bit);
+                    }
+                }
+                acc.template pairs<kGather>(v, pi, i, jj, ns - k0, 1);
             }
         }
-        size_t N = (size_t)v.N;
         if (FP32) {
             long long *F = (long long *)v.F;
+            FixedAcc fx;
+            fx.zero();
+            float f[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f[a] = __fmaf_rn(s32, acc.f32[1][a], acc.f32[0][a]);
+            fx.add(f[0], f[1], f[2], fmaxf(fabsf(f[0]), fmaxf(fabsf(f[1]), fabsf(f[2]))));
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                q[a] = acc.value(a);
-                F[a * N + i] = q[a];
+                qv[a] = fx.value(a);
+                F[a * N + i] = qv[a];
             }
             if (ENERGY) {
-                e_i = 0.5 * ((double)e_c + (double)s32 * (double)e_s);
-                w_i = 0.5 * ((double)w_c + (double)s32 * (double)w_s);
+                e_i = 0.5 * ((double)acc.e32[0] + (double)s32 * (double)acc.e32[1]);
+                w_i = 0.5 * ((double)acc.w32[0] + (double)s32 * (double)acc.w32[1]);
             }
         } else {
             double *F = (double *)v.F;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                f64[a] = fc[a] + s64 * fs[a];
+                f64[a] = acc.f64[0][a] + s64 * acc.f64[1][a];
                 F[a * N + i] = f64[a];
             }
-            e_i = 0.5 * (e_c64 + s64 * e_s64);
-            w_i = 0.5 * (w_c64 + s64 * w_s64);
+            e_i = 0.5 * (acc.e64[0] + s64 * acc.e64[1]);
+            w_i = 0.5 * (acc.w64[0] + s64 * acc.w64[1]);
         }
     }
     // Total force and energy/virial partials.
@@ -182,16 +327,16 @@ __global__ void __launch_bounds__(kBlock) k_force(View v, int step_offset)
         int lane = threadIdx.x & 31;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            long long s = warp_sum(q[a]);
+            long long s = warp_sum(qv[a]);
             if (lane == 0 && s != 0) atomicAdd(&v.sc->fsum_q[a], (unsigned long long)s);
         }
         if (ENERGY) {
             double x[2] = {e_i, w_i};
-            block_sum_d<2>(x, v.partials + (size_t)blockIdx.x * 8 + 3);
+            block_sum_d<2, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8 + 3);
         }
     } else {
         double x[5] = {f64[0], f64[1], f64[2], e_i, w_i};
-        block_sum_d<5>(x, v.partials + (size_t)blockIdx.x * 8);
+        block_sum_d<5, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8);
     }
 }
 
@@ -252,16 +397,31 @@ __global__ void k_store_forces(View v, double *out)
     }
 }
 
-// Batch positions B(i) for `step` (parity hook): out_pos[i][p] (row positions,
-// draw order), out_n[i].
-__global__ void k_batch(View v, unsigned long long step, int *out_pos, int *out_n)
+// Batch B(i) for `step` (parity hook): out_j[i][p] = neighbour indices in ascending
+// row position, out_n[i] = their number.
+__global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
-    int ns = min(v.n_shell[i], v.cap_s);
+    const size_t N = (size_t)v.N;
+    const int4 pi = v.pos[i];
+    const int ns = v.n_shell[i];
     int S[kMaxP];
-    int nb = floyd_positions(v.seed, step, v.pos[i].w, ns, v.p, S, &v.sc->flags);
-    for (int q = 0; q < nb; ++q) out_pos[(size_t)i * v.p + q] = S[q];
+    const int nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+    sort_small(S, nb);
+    const int hc = v.hcell[i];
+    SegCursor cur;
+    cur.init(v, v.start, v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1), hc);
+    int q = 0, seen = 0;
+    for (int w = 0; q < nb; ++w) {
+        const unsigned word = v.mask[(size_t)w * N + i];
+        const int cnt = __popc(word);
+        while (q < nb && S[q] < seen + cnt) {
+            out_j[(size_t)i * v.p + q] = cur.index_of(v, (w << 5) + select_bit(word, S[q] - seen));
+            ++q;
+        }
+        seen += cnt;
+    }
     out_n[i] = nb;
 }
 
@@ -270,52 +430,69 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
-    int4 pi = v.pos[i];
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 0 && v.full_list) continue;
-        const int *row = pass == 0 ? v.core + (size_t)i * v.cap_c : v.shell + (size_t)i * v.cap_s;
-        int n = pass == 0 ? min(v.n_core[i], v.cap_c) : min(v.n_shell[i], v.cap_s);
-        for (int k = 0; k < n; ++k) {
-            PairGeom g = pair_geom(pi, v.pos[row[k]], v.h);
-            bool in;
-            if (v.full_list) in = g.r2 < v.t_rs2;
-            else in = pass == 0 ? g.r2 < v.t_rc2 : (g.r2 >= v.t_rc2 && g.r2 < v.t_rs2);
-            if (!in) continue;
-            float qf = __fdiv_rn(__fsqrt_rn(g.r2), dr);
-            if (qf < (float)nbins) atomicAdd(&hist[(int)qf], 1ull);
+    const size_t N = (size_t)v.N;
+    const int4 pi = v.pos[i];
+    auto count = [&](int j, bool core_part) {
+        PairGeom g = pair_geom(pi, v.pos[j], v.h);
+        bool in;
+        if (v.full_list) in = g.r2 < v.t_rs2;
+        else in = core_part ? g.r2 < v.t_rc2 : (g.r2 >= v.t_rc2 && g.r2 < v.t_rs2);
+        if (!in) return;
+        float qf = __fdiv_rn(__fsqrt_rn(g.r2), dr);
+        if (qf < (float)nbins) atomicAdd(&hist[(int)qf], 1ull);
+    };
+    if (!v.full_list) {
+        int nc = min(v.n_core[i], v.cap_c);
+        for (int k = 0; k < nc; ++k) count(v.core[(size_t)k * N + i], true);
+    }
+    const int hc = v.hcell[i];
+    SegCursor cur;
+    cur.init(v, v.start, v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1), hc);
+    int left = v.n_shell[i];
+    for (int w = 0; left > 0; ++w) {
+        unsigned word = v.mask[(size_t)w * N + i];
+        left -= __popc(word);
+        while (word) {
+            int bit = __ffs(word) - 1;
+            word &= word - 1u;
+            count(cur.index_of(v, (w << 5) + bit), false);
         }
     }
 }
 
 } // namespace
 
-cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s)
+template <int MODE, bool FP32, bool ENERGY>
+cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kBlock);
-    bool fp32 = v.precision == RBL_FP32;
-    if (v.full_list) {
-        if (fp32) {
-            if (energy) k_force<1, true, true><<<g, kBlock, 0, s>>>(v, step_offset);
-            else k_force<1, true, false><<<g, kBlock, 0, s>>>(v, step_offset);
-        } else {
-            k_force<1, false, true><<<g, kBlock, 0, s>>>(v, step_offset);
-        }
+    int g = ceil_div(v.N, kForceThreads);
+    if constexpr (MODE == 1) {
+        k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
     } else {
-        if (fp32) {
-            if (energy) k_force<0, true, true><<<g, kBlock, 0, s>>>(v, step_offset);
-            else k_force<0, true, false><<<g, kBlock, 0, s>>>(v, step_offset);
-        } else {
-            k_force<0, false, true><<<g, kBlock, 0, s>>>(v, step_offset);
-        }
+        if (v.p > 32) k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
+        else if (v.p <= 16) k_force<MODE, FP32, ENERGY, 16><<<g, kForceThreads, 0, s>>>(v, step_offset);
+        else k_force<MODE, FP32, ENERGY, 32><<<g, kForceThreads, 0, s>>>(v, step_offset);
     }
     return cudaGetLastError();
 }
 
+cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s)
+{
+    bool fp32 = v.precision == RBL_FP32;
+    if (v.full_list) {
+        if (!fp32) return launch_force_p<1, false, true>(v, step_offset, s);
+        return energy ? launch_force_p<1, true, true>(v, step_offset, s) : launch_force_p<1, true, false>(v, step_offset, s);
+    }
+    if (!fp32) return launch_force_p<0, false, true>(v, step_offset, s);
+    return energy ? launch_force_p<0, true, true>(v, step_offset, s) : launch_force_p<0, true, false>(v, step_offset, s);
+}
+
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kBlock);
+    int g = ceil_div(v.N, kForceThreads);
     bool fp32 = v.precision == RBL_FP32;
-    k_force_finish<<<1, 1024, 0, s>>>(v, g, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance);
+    int threads = (fp32 && !energy) ? 32 : 1024;
+    k_force_finish<<<1, threads, 0, s>>>(v, g, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance);
     return cudaGetLastError();
 }
 
@@ -332,9 +509,9 @@ cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const View &v, unsigned long long step, int *out_pos, int *out_n, cudaStream_t s)
+cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s)
 {
-    k_batch<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, step, out_pos, out_n);
+    k_batch<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, step, out_j, out_n);
     return cudaGetLastError();
 }
 

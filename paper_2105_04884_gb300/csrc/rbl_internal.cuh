@@ -17,6 +17,7 @@ namespace rbl {
 constexpr int kMaxP = 64;          // largest batch size
 constexpr int kCellCap = 64;       // cells up to this size are sorted in local memory
 constexpr int kBlock = 256;        // threads per block of the per-particle kernels
+constexpr int kMinBlock = 64;      // smallest per-particle block: sizes the per-block partials
 constexpr int kMaxStencil = 7;     // offsets per axis for K <= 3
 
 // Device flags (bit positions in DevScalars::flags).
@@ -32,6 +33,7 @@ struct DevScalars {
     unsigned flags;                 // kFlag* bits
     int rebuild;                    // 1 when lists must be rebuilt before the next force
     int nc_max, ns_max;             // longest rows at the last build (even past capacity)
+    int m_max;                      // largest stencil population at the last build
     unsigned long long ns_sum;      // total shell (or full) entries at the last build
     unsigned long long nc_sum;      // total core entries at the last build
     long long n_rebuild;            // builds so far
@@ -39,8 +41,21 @@ struct DevScalars {
 };
 
 // Kernel-visible view of a context (passed by value).
+//
+// Neighbour storage.  All particles of a home cell share one candidate sequence:
+// the members of the cells of its stencil in canonical order (stencil slots
+// z-major, x-minor; members of a cell in tag order).  Along x the stencil cells of
+// one (y, z) offset are adjacent in memory, so the sequence is S = nofs_y * nofs_z
+// "segments", each one contiguous run of particle indices, or two when it wraps
+// around the periodic x face.  Per home cell, seg_prefix[c][s] is the number of
+// candidates before segment s (seg_prefix[c][S] = M_c).  Per particle:
+//   core  : explicit list of neighbour indices, column-major core[k][N];
+//   shell : bitmask over the candidate sequence, column-major mask[w][N], bit b of
+//           word w <-> candidate 32 w + b (full list in full_list mode).
+// A shell row in canonical order is the candidate sequence filtered by the mask, so
+// the position of a neighbour in its row is its rank among the set bits.
 struct View {
-    int N, p, K, cap_c, cap_s, full_list, precision, subtract;
+    int N, p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
     int ncell, n[3], nofs[3], ofs[3][kMaxStencil];
     double L[3], inv[3];            // inv = 2^32 / L
     float h[3];                     // L / 2^32 in binary32
@@ -48,7 +63,7 @@ struct View {
     double dt, T, gamma, c1;
     float c2f;                      // sqrt((1 - c1^2) T) in binary32
     unsigned long long seed;
-    // state (cell order); [buffer][axis][N] for x and v
+    // state (cell order); [axis][N] for x and v
     double *x, *v;                  // current buffer base (3 consecutive N-arrays each)
     double *x_alt, *v_alt;          // other buffer (permutation target)
     int *tag, *tag_alt;
@@ -57,11 +72,117 @@ struct View {
     void *F;                        // [3][N]: int64 fixed point (FP32 path) or double
     int *cell, *order;
     int *counts, *start, *fill, *blocksums;
-    int *core, *n_core, *shell, *n_shell;
+    int *seg_prefix;                // [ncell][S + 1]
+    int *core, *n_core;             // core[k * N + i], k < cap_c
+    unsigned *mask;                 // mask[w * N + i], w < W
+    int *n_shell;                   // set bits in the mask (N_s, or full-list length)
+    int *hcell;                     // home cell (packed) of each particle at the last build
     double *partials;               // [nblk][8]
     DevScalars *sc;
-    double *staging;                // [2][N][3] doubles for host/device I/O
+    double *staging;                // host/device I/O scratch
 };
+
+// Wrap a cell coordinate into [0, n) for -n <= c < 2n (stencil offsets never
+// reach further): compare-and-add instead of an integer division.
+__host__ __device__ __forceinline__ int wrap_cell(int c, int n)
+{
+    c = c >= n ? c - n : c;
+    return c < 0 ? c + n : c;
+}
+
+// Home cells are stored packed as cx | cy << 10 | cz << 20 (at most 1024 cells
+// per axis), so no kernel divides to recover the coordinates.
+constexpr int kCellBits = 10;
+__host__ __device__ __forceinline__ int pack_cell(int cx, int cy, int cz)
+{
+    return cx | (cy << kCellBits) | (cz << (2 * kCellBits));
+}
+
+// Linear index of a packed cell.
+__host__ __device__ __forceinline__ int cell_index(const View &v, int packed)
+{
+    const int m = (1 << kCellBits) - 1;
+    return ((packed >> (2 * kCellBits)) * v.n[1] + ((packed >> kCellBits) & m)) * v.n[0] + (packed & m);
+}
+
+// Streams the segments of a home cell in ascending candidate order and maps a
+// candidate index to a particle index.
+struct SegCursor {
+    int cx, cy, cz;       // home cell coordinates
+    const int *prefix;    // seg_prefix row of the home cell
+    const int *start;     // cell start offsets
+    int seg, oy, oz;      // current segment
+    int pre, pre_next;    // prefix[seg], prefix[seg + 1]
+    int startA, lenA, startB;
+
+    __host__ __device__ __forceinline__ void load(const View &v)
+    {
+        int czz = wrap_cell(cz + v.ofs[2][oz], v.n[2]);
+        int cyy = wrap_cell(cy + v.ofs[1][oy], v.n[1]);
+        int rowbase = (czz * v.n[1] + cyy) * v.n[0];
+        int fx = wrap_cell(cx + v.ofs[0][0], v.n[0]);
+        int last = fx + v.nofs[0] - 1;
+        int lastA = last < v.n[0] ? last : v.n[0] - 1;
+        startA = start[rowbase + fx];
+        lenA = start[rowbase + lastA + 1] - startA;
+        startB = start[rowbase];
+        pre_next = prefix[seg + 1];
+    }
+    // packed: home cell as pack_cell(cx, cy, cz); prefixp: its seg_prefix row
+    __host__ __device__ __forceinline__ void init(const View &v, const int *startp, const int *prefixp, int packed)
+    {
+        const int m = (1 << kCellBits) - 1;
+        cx = packed & m;
+        cy = (packed >> kCellBits) & m;
+        cz = packed >> (2 * kCellBits);
+        start = startp;
+        prefix = prefixp;
+        seg = oy = oz = 0;
+        pre = 0;
+        load(v);
+    }
+    // cand must not decrease between calls.
+    __host__ __device__ __forceinline__ int index_of(const View &v, int cand)
+    {
+        if (cand >= pre_next) {
+            do {
+                ++seg;
+                if (++oy == v.nofs[1]) {
+                    oy = 0;
+                    ++oz;
+                }
+                pre = pre_next;
+                pre_next = prefix[seg + 1];
+            } while (cand >= pre_next);
+            load(v);
+        }
+        int off = cand - pre;
+        return off < lenA ? startA + off : startB + (off - lenA);
+    }
+};
+
+// Position (0..31) of the r-th (0-based) set bit of w; w must have more than r bits.
+__host__ __device__ __forceinline__ int select_bit(unsigned w, int r)
+{
+#ifdef __CUDA_ARCH__
+#define RBL_POPC(x) __popc(x)
+#else
+#define RBL_POPC(x) __builtin_popcount(x)
+#endif
+    int pos = 0;
+    int c = RBL_POPC(w & 0xFFFFu);
+    if (r >= c) { r -= c; pos = 16; }
+    c = RBL_POPC((w >> pos) & 0xFFu);
+    if (r >= c) { r -= c; pos += 8; }
+    c = RBL_POPC((w >> pos) & 0xFu);
+    if (r >= c) { r -= c; pos += 4; }
+    c = RBL_POPC((w >> pos) & 0x3u);
+    if (r >= c) { r -= c; pos += 2; }
+    c = (int)((w >> pos) & 1u);
+    if (r >= c) pos += 1;
+    return pos;
+#undef RBL_POPC
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): published multipliers and
@@ -154,6 +275,68 @@ __device__ __forceinline__ int floyd_positions(unsigned long long seed, unsigned
     return p;
 }
 
+// Register-resident batch for p <= PMAX (a power of two): the Floyd positions,
+// sorted ascending and padded with INT_MAX; returns min(N_s, p).  Fast path: draw
+// q uses word q of the stream.  A draw whose low word lies below its bound could be
+// rejected by Lemire's rule and would shift the stream; the batch is then redrawn
+// by floyd_positions (the general sampler), so both paths give identical batches.
+template <int PMAX>
+__device__ __forceinline__ int batch_sorted(unsigned long long seed, unsigned long long step, int tag, int ns,
+                                            int p, int (&S)[PMAX], unsigned *flags)
+{
+    const int kInf = 0x7fffffff;
+    if (ns <= p) {
+#pragma unroll
+        for (int q = 0; q < PMAX; ++q) S[q] = q < ns ? q : kInf;
+        return ns;
+    }
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c0 = (uint32_t)step, c1 = (uint32_t)(step >> 32);
+    bool slow = false;
+    uint4 blk = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+        if (q < p) {
+            if ((q & 3) == 0) blk = philox4x32_10(make_uint4(c0, c1, (uint32_t)tag, (uint32_t)(q >> 2)), k0, k1);
+            const uint32_t w = (q & 3) == 0 ? blk.x : (q & 3) == 1 ? blk.y : (q & 3) == 2 ? blk.z : blk.w;
+            const uint32_t bound = (uint32_t)(ns - p + q) + 1u;
+            const unsigned long long m = (unsigned long long)w * bound;
+            slow |= (uint32_t)m < bound;
+            const int t = (int)(m >> 32);
+            bool seen = false;
+#pragma unroll
+            for (int r = 0; r < q; ++r) seen |= (S[r] == t);
+            S[q] = seen ? (int)(bound - 1u) : t;
+        } else {
+            S[q] = kInf;
+        }
+    }
+    if (slow) {
+        int T[kMaxP];
+        const int nb = floyd_positions(seed, step, tag, ns, p, T, flags);
+#pragma unroll
+        for (int q = 0; q < PMAX; ++q) S[q] = q < nb ? T[q] : kInf;
+    }
+    // bitonic sort network on registers
+#pragma unroll
+    for (int k = 2; k <= PMAX; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int a = 0; a < PMAX; ++a) {
+                const int b = a ^ j;
+                if (b > a) {
+                    const int x = S[a], y = S[b];
+                    const bool up = (a & k) == 0;
+                    S[a] = up ? min(x, y) : max(x, y);
+                    S[b] = up ? max(x, y) : min(x, y);
+                }
+            }
+        }
+    }
+    return p;
+}
+
 // ---------------------------------------------------------------------------
 // Canonical pair rule: d = (float)(int32)(u_i - u_j) * h, r2 = (dx dx + dy dy) + dz dz,
 // every operation rounded separately.
@@ -179,10 +362,19 @@ __device__ __forceinline__ int cell_coord(unsigned u, int n)
 }
 
 // LJ 12-6 in binary32: returns the force coefficient fmag with f = fmag * d, and
-// the pair energy / virial when asked.
+// the pair energy / virial when asked.  1/r^2 comes from the hardware reciprocal
+// (rcp.approx, within 1 ulp); every path that must agree bit for bit (RBL with the
+// whole shell, the full list) goes through this same function.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float lj_coef(float r2, float *u, float *w)
 {
-    float inv = __frcp_rn(r2);
+    float inv = rcp_approx(r2);
     float r6 = __fmul_rn(__fmul_rn(inv, inv), inv);
     float t = __fmaf_rn(2.0f, r6, -1.0f);         // 2 r^-6 - 1
     float vir = __fmul_rn(__fmul_rn(24.0f, r6), t); // 24 (2 r^-12 - r^-6) = r . f
@@ -193,10 +385,12 @@ __device__ __forceinline__ float lj_coef(float r2, float *u, float *w)
 
 // ---------------------------------------------------------------------------
 // Exact fixed-point accumulation of binary32 values at scale 2^24.  Each value f
-// (|f| < 2^20) is split without rounding error into A = rint(4f) and
+// with |f| < 2^20 is split without rounding error into A = rint(4f) and
 // B = rint((4f - A) 2^22), so rint(f 2^24) = A 2^22 + B; A and B are summed as
 // 32-bit integers (order-independent, exact), using the 1.5 * 2^23 bias trick so
-// that both conversions are single binary32 operations.
+// that both conversions are single binary32 operations.  For 2^20 <= |f| < 2^29
+// (nearly overlapping pairs) the same split is taken with exact integer
+// conversions (4f - rint(4f) is 0 or 1/2 there).
 // ---------------------------------------------------------------------------
 struct FixedAcc {
     unsigned a[3], b[3];
@@ -206,7 +400,7 @@ struct FixedAcc {
         a[0] = a[1] = a[2] = b[0] = b[1] = b[2] = 0u;
         n = 0;
     }
-    __device__ __forceinline__ void add1(int k, float f)
+    __device__ __forceinline__ void add1_small(int k, float f)
     {
         const float M = 12582912.0f; // 1.5 * 2^23
         float y = __fmaf_rn(f, 4.0f, M);
@@ -216,11 +410,27 @@ struct FixedAcc {
         a[k] += __float_as_uint(y);
         b[k] += __float_as_uint(z);
     }
-    __device__ __forceinline__ void add(float fx, float fy, float fz)
+    __device__ __forceinline__ void add1_large(int k, float f)
     {
-        add1(0, fx);
-        add1(1, fy);
-        add1(2, fz);
+        const unsigned bias = 0x4B400000u;
+        float g = fminf(fmaxf(__fmul_rn(f, 4.0f), -2147483520.0f), 2147483520.0f);
+        float y = rintf(g);                      // exact
+        float r = __fsub_rn(g, y);               // 0 or +-1/2, exact
+        a[k] += (unsigned)__float2int_rn(y) + bias;
+        b[k] += (unsigned)__float2int_rn(__fmul_rn(r, 4194304.0f)) + bias;
+    }
+    // m: an upper bound of max(|fx|, |fy|, |fz|)
+    __device__ __forceinline__ void add(float fx, float fy, float fz, float m)
+    {
+        if (m < 1048576.0f) {
+            add1_small(0, fx);
+            add1_small(1, fy);
+            add1_small(2, fz);
+        } else {
+            add1_large(0, fx);
+            add1_large(1, fy);
+            add1_large(2, fz);
+        }
         ++n;
     }
     // Exact int64 value of the sum at scale 2^24 for component k.
@@ -263,12 +473,24 @@ __device__ __forceinline__ unsigned quantize(double x, double inv)
     return (unsigned)(unsigned long long)__double_as_longlong(y);
 }
 
-// Wrap into [0, L) for a particle that moved by less than L.
+// Wrap into [0, L) for a particle that moved by less than L.  The comparisons are
+// done on the IEEE bit patterns (integer units) instead of the FP64 pipe: for
+// x >= 0 the order of the patterns is the order of the values.
 __device__ __forceinline__ double wrap(double x, double L)
 {
-    if (x < 0.0) x += L;
-    if (x >= L) x -= L;
+    long long b = __double_as_longlong(x);
+    if (b < 0) {                 // sign bit: x < 0 (or -0.0)
+        x += L;
+        b = __double_as_longlong(x);
+    }
+    if (b >= __double_as_longlong(L)) x -= L;
     return x;
+}
+
+// Not NaN/inf, from the exponent bits.
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
 }
 
 inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
@@ -302,12 +524,13 @@ namespace rbl {
 cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s);
 cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s);
 cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s);
+cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
 cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s);
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
 cudaError_t launch_kinetic(const View &v, cudaStream_t s);
-cudaError_t launch_batch(const View &v, unsigned long long step, int *out_pos, int *out_n, cudaStream_t s);
+cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
 } // namespace rbl

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double xa = wrap(xx[a], v.L[a]);
-        bad |= !(xa >= 0.0 && xa < v.L[a]) || !isfinite(vv[a]);
+        bad |= !finite_bits(xa) || !finite_bits(vv[a]);
         v.x[a * N + i] = xa;
         v.v[a * N + i] = vv[a];
         u[a] = quantize(xa, v.inv[a]);

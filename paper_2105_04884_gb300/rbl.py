@@ -32,7 +32,7 @@ class rbl_params(ctypes.Structure):
                 ("skin", ctypes.c_double), ("p", ctypes.c_int), ("dt", ctypes.c_double), ("T", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int),
                 ("full_list", ctypes.c_int), ("subtract_net_force", ctypes.c_int),
-                ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_shell", ctypes.c_int)]
+                ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_stencil", ctypes.c_int)]
 
 
 class rbl_obs(ctypes.Structure):
@@ -101,7 +101,7 @@ def load(build_if_missing: bool = False):
 
 
 def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32, full_list=False,
-                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_shell=0) -> rbl_params:
+                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0) -> rbl_params:
     prm = rbl_params()
     load().rbl_params_default(ctypes.byref(prm))
     Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
@@ -113,7 +113,7 @@ def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RB
     prm.full_list = int(bool(full_list))
     prm.subtract_net_force = int(bool(subtract_net_force))
     prm.cells_per_cutoff = int(cells_per_cutoff)
-    prm.cap_core, prm.cap_shell = int(cap_core), int(cap_shell)
+    prm.cap_core, prm.cap_stencil = int(cap_core), int(cap_stencil)
     return prm
 
 
@@ -129,7 +129,7 @@ class System:
     """One RBL (or full-list) system on the current CUDA device and stream."""
 
     def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
-                 full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_shell=0, step=0,
+                 full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
                  stream=None, device=None):
         import torch
 
@@ -138,7 +138,7 @@ class System:
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
         self.N = int(x.shape[0])
         self.prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
-                               cells_per_cutoff, cap_core, cap_shell)
+                               cells_per_cutoff, cap_core, cap_stencil)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         # a stream of its own (the legacy default stream cannot host graph replays)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
