@@ -167,6 +167,27 @@ rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
 rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable);
 rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int reset);
 
+/* Allocation-free force evaluation (the paper has no counterpart; this is a service
+ * for callers that may not allocate).  Some callers cannot allocate device memory
+ * when they need forces: a plugin called inside another engine's time step whose
+ * host application owns all device memory through its own pool and forbids
+ * cudaMalloc (it can fail or synchronise the device mid-run), or code bound by a
+ * no-allocation rule after initialisation.  This call computes, like rbl_forces on
+ * a fresh context, the mean-subtracted RBL (or full-list) force of positions
+ * x[N][3] (device pointer, tag order) at step counter `step` into F[N][3] (device
+ * pointer, tag order), on `stream`, and synchronises that stream.  It allocates
+ * nothing: its working memory is one file-scope device array of 48 MiB, which every
+ * device where the library's module is loaded (at the latest on the first call of
+ * this function there) holds until the process exits.  The first call on a device,
+ * made with that device current, looks up the array's device address; make that
+ * first call before any stream capture.  Systems whose workspace (as
+ * rbl_workspace_size reports) exceeds 48 MiB are rejected with RBL_ENOMEM (about
+ * 60,000 particles at rho* = 0.8 with the default radii); invalid parameters with
+ * RBL_EINVAL.  Every call shares the array, so calls that overlap on the GPU (two
+ * streams, two host threads) race: serialise them.  Each call resets the parts it
+ * reads; the array keeps the last call's contents otherwise. */
+rbl_status rbl_forces_static(const rbl_params *prm, int N, const double *x, long long step, double *F, void *stream);
+
 /* Releases the handle (the workspace stays the caller's). NULL is ignored. */
 void rbl_destroy(rbl_ctx *ctx);
 

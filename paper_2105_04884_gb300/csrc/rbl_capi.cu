@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "rbl_internal.cuh"
@@ -706,3 +707,139 @@ const char *rbl_status_string(rbl_status s)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free force evaluation.
+//
+// Some callers cannot allocate device memory at the point where they need forces:
+// a plugin called from inside another engine's time step, where the host
+// application owns all device memory through its own pool and forbids cudaMalloc
+// (which can fail or synchronise the device mid-run), or code that runs after its
+// initialisation phase under a no-allocation rule.  rbl_forces_static serves them:
+// every array it needs lives in one file-scope device array of fixed size, loaded
+// with the library, so the call allocates nothing, host or device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)48 << 20; // 48 MiB, held by every device that loads the library
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_ptr[kMaxDevices]; // device address of g_static_scratch, per device ordinal
+
+// Device address of the scratch array on the current device.  The host-side name
+// g_static_scratch is only a stand-in; the address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+rbl_status static_scratch_address(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RBL_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return RBL_EINVAL;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return RBL_ECUDA;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return RBL_OK;
+}
+
+// View over a laid-out region starting at base (same carving as a context's workspace).
+void static_view(View &v, const rbl_params *prm, int N, const Layout &L, char *base)
+{
+    v = View{};
+    v.N = N;
+    v.p = prm->p;
+    v.K = prm->cells_per_cutoff;
+    v.cap_c = L.cap_c;
+    v.W = L.W;
+    v.S = L.S;
+    v.Mcap = L.Mcap;
+    v.full_list = prm->full_list ? 1 : 0;
+    v.precision = prm->precision;
+    v.subtract = prm->subtract_net_force ? 1 : 0;
+    v.ncell = L.ncell;
+    for (int a = 0; a < 3; ++a) {
+        int n = L.n3[a], K = prm->cells_per_cutoff;
+        v.n[a] = n;
+        v.nofs[a] = L.nofs3[a];
+        for (int o = 0; o < L.nofs3[a]; ++o) v.ofs[a][o] = n >= 2 * K + 1 ? o - K : o;
+        v.L[a] = prm->L[a];
+        v.inv[a] = 4294967296.0 / prm->L[a];
+        v.h[a] = (float)(prm->L[a] / 4294967296.0);
+    }
+    double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
+    double lo = rc - sk > 0.0 ? rc - sk : 0.0;
+    v.t_core_list = (float)((rc + sk) * (rc + sk));
+    v.t_shell_lo = (float)(lo * lo);
+    v.t_cut_list = (float)((rs + sk) * (rs + sk));
+    v.t_rc2 = (float)(rc * rc);
+    v.t_rs2 = (float)(rs * rs);
+    v.t_disp = (float)(0.25 * sk * sk);
+    v.dt = prm->dt;
+    v.T = prm->T;
+    v.gamma = prm->gamma;
+    v.c1 = std::exp(-prm->gamma * prm->dt);
+    v.c2f = (float)std::sqrt((1.0 - v.c1 * v.c1) * prm->T);
+    v.seed = prm->seed;
+    int k = 0;
+    v.x = (double *)(base + L.off[k++]);
+    v.x_alt = (double *)(base + L.off[k++]);
+    v.v = (double *)(base + L.off[k++]);
+    v.v_alt = (double *)(base + L.off[k++]);
+    v.tag = (int *)(base + L.off[k++]);
+    v.tag_alt = (int *)(base + L.off[k++]);
+    v.pos = (int4 *)(base + L.off[k++]);
+    v.pos_alt = (int4 *)(base + L.off[k++]);
+    v.ubuild = (int4 *)(base + L.off[k++]);
+    v.F = (void *)(base + L.off[k++]);
+    v.cell = (int *)(base + L.off[k++]);
+    v.order = (int *)(base + L.off[k++]);
+    v.counts = (int *)(base + L.off[k++]);
+    v.start = (int *)(base + L.off[k++]);
+    v.fill = (int *)(base + L.off[k++]);
+    v.blocksums = (int *)(base + L.off[k++]);
+    v.seg_prefix = (int *)(base + L.off[k++]);
+    v.core = (int *)(base + L.off[k++]);
+    v.n_core = (int *)(base + L.off[k++]);
+    v.mask = (unsigned *)(base + L.off[k++]);
+    v.n_shell = (int *)(base + L.off[k++]);
+    v.hcell = (int *)(base + L.off[k++]);
+    v.partials = (double *)(base + L.off[k++]);
+    v.sc = (DevScalars *)(base + L.off[k++]);
+    v.staging = (double *)(base + L.off[k++]);
+}
+
+} // namespace
+
+extern "C" rbl_status rbl_forces_static(const rbl_params *prm, int N, const double *x, long long step, double *F,
+                                        void *stream)
+{
+    if (!x || !F || step < 0) return RBL_EINVAL;
+    rbl_status st = validate(prm, N, nullptr, 0);
+    if (st != RBL_OK) return st;
+    const Layout L = make_layout(prm, N);
+    if (L.total > kStaticScratchBytes) return RBL_ENOMEM;
+    void *base = nullptr;
+    st = static_scratch_address(&base);
+    if (st != RBL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    View v;
+    static_view(v, prm, N, L, (char *)base);
+    // the array keeps the previous call's contents: reset the scalars this call reads
+    DevScalars h{};
+    h.step = (unsigned long long)step;
+    if (cudaMemcpyAsync(v.sc, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, s) != cudaSuccess) return RBL_ECUDA;
+    if (launch_load_state(v, x, nullptr, s) != cudaSuccess) return RBL_ECUDA;
+    if (launch_rebuild(v, L.ntiles, false, s) != cudaSuccess) return RBL_ECUDA;
+    if (launch_forces(v, 0, 0, false, s) != cudaSuccess) return RBL_ECUDA;
+    if (launch_store_forces(v, F, s) != cudaSuccess) return RBL_ECUDA;
+    if (cudaMemcpyAsync(&h, v.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RBL_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RBL_ECUDA;
+    if (h.flags & (kFlagOverflow | kFlagCellOverflow)) return RBL_EOVERFLOW;
+    if (h.flags & kFlagNonFinite) return RBL_ENONFINITE;
+    if (h.flags & kFlagRngLimit) return RBL_ETIMEOUT;
+    return RBL_OK;
+}

@@ -50,8 +50,8 @@ class rbl_obs(ctypes.Structure):
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_create", "rbl_set_state", "rbl_get_state",
            "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_get_lists", "rbl_get_batch",
-           "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_destroy", "rbl_last_error",
-           "rbl_status_string"]
+           "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_forces_static", "rbl_destroy",
+           "rbl_last_error", "rbl_status_string"]
 
 _lib = None
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
     L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
     L.rbl_set_phase_timing.argtypes = [P, I]
     L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
+    L.rbl_forces_static.argtypes = [ctypes.POINTER(rbl_params), I, P, LL, P, P]
     L.rbl_destroy.argtypes = [P]
     L.rbl_destroy.restype = None
     L.rbl_last_error.argtypes = [P]
