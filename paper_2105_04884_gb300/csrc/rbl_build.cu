@@ -272,8 +272,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
         for (int sg = 1; sg <= S; ++sg) pre[sg] += pre[sg - 1];
     }
     __syncwarp();
-    int *gp = v.seg_prefix + (size_t)c * (S + 1);
-    for (int sg = lane; sg <= S; sg += 32) gp[sg] = pre[sg];
+    int4 *gt = v.seg_tab + (size_t)c * S;
+    for (int sg = lane; sg < S; sg += 32) gt[sg] = make_int4(sA[sg], lA[sg], sB[sg], pre[sg + 1]);
     const int s0 = v.start[c], s1 = v.start[c + 1];
     const int M = pre[S];
     if (s1 == s0) return;

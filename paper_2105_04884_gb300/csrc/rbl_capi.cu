@@ -113,7 +113,7 @@ Layout make_layout(const rbl_params *p, int N)
         4 * Nz, 4 * Nz,                             // cell, order
         4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), // counts, start, fill
         4 * ((size_t)L.ntiles + 1),                 // blocksums
-        4 * (size_t)L.ncell * (size_t)(L.S + 1),    // seg_prefix
+        16 * (size_t)L.ncell * (size_t)L.S,         // seg_tab
         4 * Nz * (size_t)L.cap_c, 4 * Nz,           // core, n_core
         4 * Nz * (size_t)L.W, 4 * Nz,               // mask, n_shell
         4 * Nz,                                     // hcell
@@ -382,7 +382,7 @@ rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t work
     v.start = (int *)(base + L.off[k++]);
     v.fill = (int *)(base + L.off[k++]);
     v.blocksums = (int *)(base + L.off[k++]);
-    v.seg_prefix = (int *)(base + L.off[k++]);
+    v.seg_tab = (int4 *)(base + L.off[k++]);
     v.core = (int *)(base + L.off[k++]);
     v.n_core = (int *)(base + L.off[k++]);
     v.mask = (unsigned *)(base + L.off[k++]);
@@ -587,25 +587,24 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
     }
     // decode the masks on the host with the same segment walk as the kernels
     std::vector<unsigned> mask(N * (size_t)v.W);
-    std::vector<int> start((size_t)v.ncell + 1), prefix((size_t)v.ncell * (v.S + 1));
+    std::vector<int4> tab((size_t)v.ncell * v.S);
     std::vector<int> hcell(N);
     CK(cudaMemcpy(mask.data(), v.mask, mask.size() * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(start.data(), v.start, start.size() * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(prefix.data(), v.seg_prefix, prefix.size() * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tab.data(), v.seg_tab, tab.size() * 16, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hcell.data(), v.hcell, 4 * N, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < N; ++i) {
         int t = tag[i];
         counts[t] = cnt[i];
         int c = cell_index(v, hcell[i]);
         SegCursor cur;
-        cur.init(v, start.data(), prefix.data() + (size_t)c * (v.S + 1), hcell[i]);
+        cur.init(tab.data() + (size_t)c * v.S);
         int k = 0;
         for (int w = 0; w < v.W && k < cnt[i]; ++w) {
             unsigned word = mask[(size_t)w * N + i];
             while (word) {
                 int bit = __builtin_ctz(word);
                 word &= word - 1u;
-                rows[(size_t)t * cap + k++] = tag[cur.index_of(v, (w << 5) + bit)];
+                rows[(size_t)t * cap + k++] = tag[cur.index_of((w << 5) + bit)];
             }
         }
     }
@@ -801,7 +800,7 @@ void static_view(View &v, const rbl_params *prm, int N, const Layout &L, char *b
     v.start = (int *)(base + L.off[k++]);
     v.fill = (int *)(base + L.off[k++]);
     v.blocksums = (int *)(base + L.off[k++]);
-    v.seg_prefix = (int *)(base + L.off[k++]);
+    v.seg_tab = (int4 *)(base + L.off[k++]);
     v.core = (int *)(base + L.off[k++]);
     v.n_core = (int *)(base + L.off[k++]);
     v.mask = (unsigned *)(base + L.off[k++]);

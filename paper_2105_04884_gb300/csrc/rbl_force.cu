@@ -143,21 +143,19 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 // PMAX > 0: batch positions and neighbour indices live in registers (p <= PMAX);
 // PMAX = 0: general path through local arrays (p up to kMaxP).
 //
-// Memory-level parallelism: the core indices and the mask words of a thread are
-// staged in shared memory with bursts of independent loads (column-major storage
-// makes every burst coalesced across the warp), the batch is drawn while those
-// loads are in flight, and neighbour positions are gathered kGather at a time
-// before their pair terms are computed.
+// Memory-level parallelism: the mask words of a thread are staged in shared memory
+// with bursts of independent loads (column-major storage makes every burst coalesced
+// across the warp), the batch is drawn while those loads are in flight, and
+// neighbour indices and positions are gathered kGather at a time before their pair
+// terms are computed.
 constexpr int kForceThreads = 128;
 static_assert(kForceThreads >= kMinBlock, "per-block partials are sized for kMinBlock");
-constexpr int kCoreStage = 32;  // core entries staged per thread (longer rows read directly)
-constexpr int kMaskStage = 40;  // mask words staged per thread
+constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
 constexpr int kGather = 8;
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX>
 __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset)
 {
-    __shared__ int s_core[MODE == 0 ? kCoreStage : 1][kForceThreads];
     __shared__ unsigned s_mask[kMaskStage][kForceThreads];
     const unsigned long long step = v.sc->step + (unsigned long long)step_offset;
     const int t = threadIdx.x;
@@ -170,19 +168,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
         const int4 pi = v.pos[i];
         const int nc = MODE == 0 ? min(v.n_core[i], v.cap_c) : 0;
         const int ns = v.n_shell[i];
-        const int hc = v.hcell[i];
-        const int *prefix = v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1);
-        const int nwords = min((prefix[v.S] + 31) >> 5, v.W);
-        // stage core indices and mask words (independent loads, in bursts)
-        const int ncs = min(nc, kCoreStage);
-        for (int k0 = 0; k0 < ncs; k0 += 8) {
-            int tmp[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) tmp[u] = k0 + u < ncs ? v.core[(size_t)(k0 + u) * N + i] : 0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (k0 + u < ncs) s_core[k0 + u][t] = tmp[u];
-        }
+        const int4 *tab = v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S;
+        const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
+        // stage the mask words (independent loads, in bursts)
         const int nws = min(nwords, kMaskStage);
         for (int w0 = 0; w0 < nws; w0 += 8) {
             unsigned tmp[8];
@@ -198,7 +186,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
         Accum<FP32, ENERGY> acc;
         acc.zero();
         SegCursor cur;
-        cur.init(v, v.start, prefix, hc);
+        cur.init(tab);
         float s32 = 1.0f;
         double s64 = 1.0;
         if (MODE == 0) {
@@ -224,7 +212,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                             word = mask_word(++w);
                             cnt = __popc(word);
                         }
-                        J[q] = cur.index_of(v, (w << 5) + select_bit(word, tq - seen));
+                        J[q] = cur.index_of((w << 5) + select_bit(word, tq - seen));
                     }
                 }
 #pragma unroll
@@ -259,7 +247,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                                 word = mask_word(++w);
                                 cnt = __popc(word);
                             }
-                            jj[u] = cur.index_of(v, (w << 5) + select_bit(word, tq - seen));
+                            jj[u] = cur.index_of((w << 5) + select_bit(word, tq - seen));
                         }
                     }
                     acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
@@ -271,7 +259,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
 #pragma unroll
                 for (int u = 0; u < kGather; ++u) {
                     const int k = k0 + u;
-                    jj[u] = k < nc ? (k < kCoreStage ? s_core[k][t] : v.core[(size_t)k * N + i]) : i;
+                    jj[u] = k < nc ? v.core[(size_t)k * N + i] : i;
                 }
                 acc.template pairs<kGather>(v, pi, i, jj, nc - k0, 0);
             }
@@ -288,7 +276,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                         while (word == 0u) word = mask_word(++w);
                         const int bit = __ffs(word) - 1;
                         word &= word - 1u;
-                        jj[u] = cur.index_of(v, (w << 5) + bit);
+                        jj[u] = cur.index_of((w << 5) + bit);
                     }
                 }
                 acc.template pairs<kGather>(v, pi, i, jj, ns - k0, 1);
@@ -409,15 +397,14 @@ __global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
     int S[kMaxP];
     const int nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
     sort_small(S, nb);
-    const int hc = v.hcell[i];
     SegCursor cur;
-    cur.init(v, v.start, v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1), hc);
+    cur.init(v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S);
     int q = 0, seen = 0;
     for (int w = 0; q < nb; ++w) {
         const unsigned word = v.mask[(size_t)w * N + i];
         const int cnt = __popc(word);
         while (q < nb && S[q] < seen + cnt) {
-            out_j[(size_t)i * v.p + q] = cur.index_of(v, (w << 5) + select_bit(word, S[q] - seen));
+            out_j[(size_t)i * v.p + q] = cur.index_of((w << 5) + select_bit(word, S[q] - seen));
             ++q;
         }
         seen += cnt;
@@ -445,9 +432,8 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
         int nc = min(v.n_core[i], v.cap_c);
         for (int k = 0; k < nc; ++k) count(v.core[(size_t)k * N + i], true);
     }
-    const int hc = v.hcell[i];
     SegCursor cur;
-    cur.init(v, v.start, v.seg_prefix + (size_t)cell_index(v, hc) * (v.S + 1), hc);
+    cur.init(v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S);
     int left = v.n_shell[i];
     for (int w = 0; left > 0; ++w) {
         unsigned word = v.mask[(size_t)w * N + i];
@@ -455,7 +441,7 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
         while (word) {
             int bit = __ffs(word) - 1;
             word &= word - 1u;
-            count(cur.index_of(v, (w << 5) + bit), false);
+            count(cur.index_of((w << 5) + bit), false);
         }
     }
 }

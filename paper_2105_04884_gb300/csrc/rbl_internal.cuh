@@ -47,8 +47,10 @@ struct DevScalars {
 // z-major, x-minor; members of a cell in tag order).  Along x the stencil cells of
 // one (y, z) offset are adjacent in memory, so the sequence is S = nofs_y * nofs_z
 // "segments", each one contiguous run of particle indices, or two when it wraps
-// around the periodic x face.  Per home cell, seg_prefix[c][s] is the number of
-// candidates before segment s (seg_prefix[c][S] = M_c).  Per particle:
+// around the periodic x face.  Per home cell, seg_tab[c][s] = (startA, lenA, startB,
+// candidates up to and including segment s): the first piece's start and length,
+// the second piece's start, and the running count (seg_tab[c][S-1].w = M_c).
+// Per particle:
 //   core  : explicit list of neighbour indices, column-major core[k][N];
 //   shell : bitmask over the candidate sequence, column-major mask[w][N], bit b of
 //           word w <-> candidate 32 w + b (full list in full_list mode).
@@ -72,7 +74,7 @@ struct View {
     void *F;                        // [3][N]: int64 fixed point (FP32 path) or double
     int *cell, *order;
     int *counts, *start, *fill, *blocksums;
-    int *seg_prefix;                // [ncell][S + 1]
+    int4 *seg_tab;                  // [ncell][S]
     int *core, *n_core;             // core[k * N + i], k < cap_c
     unsigned *mask;                 // mask[w * N + i], w < W
     int *n_shell;                   // set bits in the mask (N_s, or full-list length)
@@ -106,58 +108,29 @@ __host__ __device__ __forceinline__ int cell_index(const View &v, int packed)
 }
 
 // Streams the segments of a home cell in ascending candidate order and maps a
-// candidate index to a particle index.
+// candidate index to a particle index: one 16-byte table load per segment.
 struct SegCursor {
-    int cx, cy, cz;       // home cell coordinates
-    const int *prefix;    // seg_prefix row of the home cell
-    const int *start;     // cell start offsets
-    int seg, oy, oz;      // current segment
-    int pre, pre_next;    // prefix[seg], prefix[seg + 1]
-    int startA, lenA, startB;
+    const int4 *tab;      // seg_tab row of the home cell
+    int seg;              // current segment
+    int pre;              // candidates before the current segment
+    int4 e;               // (startA, lenA, startB, candidates through the segment)
 
-    __host__ __device__ __forceinline__ void load(const View &v)
+    __host__ __device__ __forceinline__ void init(const int4 *tabp)
     {
-        int czz = wrap_cell(cz + v.ofs[2][oz], v.n[2]);
-        int cyy = wrap_cell(cy + v.ofs[1][oy], v.n[1]);
-        int rowbase = (czz * v.n[1] + cyy) * v.n[0];
-        int fx = wrap_cell(cx + v.ofs[0][0], v.n[0]);
-        int last = fx + v.nofs[0] - 1;
-        int lastA = last < v.n[0] ? last : v.n[0] - 1;
-        startA = start[rowbase + fx];
-        lenA = start[rowbase + lastA + 1] - startA;
-        startB = start[rowbase];
-        pre_next = prefix[seg + 1];
-    }
-    // packed: home cell as pack_cell(cx, cy, cz); prefixp: its seg_prefix row
-    __host__ __device__ __forceinline__ void init(const View &v, const int *startp, const int *prefixp, int packed)
-    {
-        const int m = (1 << kCellBits) - 1;
-        cx = packed & m;
-        cy = (packed >> kCellBits) & m;
-        cz = packed >> (2 * kCellBits);
-        start = startp;
-        prefix = prefixp;
-        seg = oy = oz = 0;
+        tab = tabp;
+        seg = 0;
         pre = 0;
-        load(v);
+        e = tab[0];
     }
     // cand must not decrease between calls.
-    __host__ __device__ __forceinline__ int index_of(const View &v, int cand)
+    __host__ __device__ __forceinline__ int index_of(int cand)
     {
-        if (cand >= pre_next) {
-            do {
-                ++seg;
-                if (++oy == v.nofs[1]) {
-                    oy = 0;
-                    ++oz;
-                }
-                pre = pre_next;
-                pre_next = prefix[seg + 1];
-            } while (cand >= pre_next);
-            load(v);
+        while (cand >= e.w) {
+            pre = e.w;
+            e = tab[++seg];
         }
         int off = cand - pre;
-        return off < lenA ? startA + off : startB + (off - lenA);
+        return off < e.y ? e.x + off : e.z + (off - e.y);
     }
 };
 
