@@ -290,8 +290,8 @@ static thresholds make_thresholds(double rc, double rs, double skin)
  * The stencil of a cell is (2K+1)^3 cells (offsets -K..K per axis), or, on an
  * axis with fewer than 2K+1 cells, every cell of that axis once (offsets
  * 0..n_a-1), visited z-major, x-minor.  Row order of a list = (stencil slot of
- * the neighbour's cell, tag): this is the canonical order in which batch
- * positions are counted.                                                        */
+ * the neighbour's cell, the neighbour's x image u_x, tag): this is the canonical
+ * order in which batch positions are counted.                                   */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int n[3];
@@ -368,6 +368,7 @@ void orc_cells(int n, const uint32_t *u, const double L[3], double rs, double sk
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int32_t slot;
+    uint32_t ux;
     int32_t tag;
 } row_key;
 
@@ -375,13 +376,16 @@ static int cmp_row_key(const void *a, const void *b)
 {
     const row_key *x = (const row_key *)a, *y = (const row_key *)b;
     if (x->slot != y->slot) return x->slot < y->slot ? -1 : 1;
+    if (x->ux != y->ux) return x->ux < y->ux ? -1 : 1;
     return (x->tag > y->tag) - (x->tag < y->tag);
 }
 
-static void sort_row(int32_t *row, int len, const cell_grid *g, const int *cells3, int i, row_key *scratch)
+static void sort_row(int32_t *row, int len, const cell_grid *g, const int *cells3, const uint32_t *u, int i,
+                     row_key *scratch)
 {
     for (int k = 0; k < len; ++k) {
         scratch[k].slot = stencil_slot(g, cells3 + 3 * i, cells3 + 3 * row[k]);
+        scratch[k].ux = u[3 * row[k]];
         scratch[k].tag = row[k];
     }
     qsort(scratch, (size_t)len, sizeof(row_key), cmp_row_key);
@@ -432,9 +436,9 @@ int orc_build_lists_brute(int n, const double *x, const double L[3], double rc, 
 #pragma omp atomic write
                 status = ORC_EOVERFLOW;
             } else {
-                sort_row(core + (size_t)i * cap_core, nc, &g, cells3, i, scratch);
-                sort_row(shell + (size_t)i * cap_shell, ns, &g, cells3, i, scratch);
-                if (full) sort_row(full + (size_t)i * cap_full, nf, &g, cells3, i, scratch);
+                sort_row(core + (size_t)i * cap_core, nc, &g, cells3, u, i, scratch);
+                sort_row(shell + (size_t)i * cap_shell, ns, &g, cells3, u, i, scratch);
+                if (full) sort_row(full + (size_t)i * cap_full, nf, &g, cells3, u, i, scratch);
             }
             n_core[i] = nc;
             n_shell[i] = ns;
@@ -474,6 +478,22 @@ int orc_build_lists_cells(int n, const double *x, const double L[3], double rc, 
         memcpy(fill, start, sizeof(int) * (size_t)ncell);
         for (int i = 0; i < n; ++i) members[fill[cell[i]]++] = i; /* ascending tag within a cell */
         free(fill);
+    }
+    /* within a cell: ascending x image, then tag */
+    {
+        row_key *keys = (row_key *)malloc(sizeof(row_key) * (size_t)(n > 0 ? n : 1));
+        for (int c = 0; c < ncell; ++c) {
+            int m = start[c + 1] - start[c];
+            for (int k = 0; k < m; ++k) {
+                int j = members[start[c] + k];
+                keys[k].slot = 0;
+                keys[k].ux = u[3 * j];
+                keys[k].tag = j;
+            }
+            qsort(keys, (size_t)m, sizeof(row_key), cmp_row_key);
+            for (int k = 0; k < m; ++k) members[start[c] + k] = keys[k].tag;
+        }
+        free(keys);
     }
     int status = ORC_OK;
 #pragma omp parallel for schedule(dynamic, 256)

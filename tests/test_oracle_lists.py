@@ -132,9 +132,9 @@ def test_list_membership_against_fp64():
         assert shell & s == want_shell & s
 
 
-def test_canonical_row_order_is_slot_then_tag():
-    """Row order: by the neighbour cell's stencil slot, then by tag (checked against a
-    direct recomputation of the slot from the cell coordinates)."""
+def test_canonical_row_order_is_slot_x_then_tag():
+    """Row order: by the neighbour cell's stencil slot, then by the neighbour's x
+    image, then by tag (checked against a direct recomputation from the cells)."""
     x, L = inputs.fcc(1000, 0.8, 0.2, seed=2)
     K = 2
     lists = oracle.build_lists(x, L, RC, RS, SKIN, K=K, method="cells")
@@ -147,12 +147,13 @@ def test_canonical_row_order_is_slot_then_tag():
         return list(range(-K, K + 1)) if n >= 2 * K + 1 else list(range(n))
 
     for i in range(0, 1000, 37):
-        keys = []
-        for j in lists.row("shell", i):
-            idx = []
-            for a in range(3):
-                offs = offsets(int(n3[a]))
-                idx.append([(c[i, a] + o) % n3[a] for o in offs].index(c[j, a]))
-            slot = (idx[2] * len(offsets(int(n3[1]))) + idx[1]) * len(offsets(int(n3[0]))) + idx[0]
-            keys.append((slot, int(j)))
-        assert keys == sorted(keys)
+        for kind in ("core", "shell", "full"):
+            keys = []
+            for j in lists.row(kind, i):
+                idx = []
+                for a in range(3):
+                    offs = offsets(int(n3[a]))
+                    idx.append([(c[i, a] + o) % n3[a] for o in offs].index(c[j, a]))
+                slot = (idx[2] * len(offsets(int(n3[1]))) + idx[1]) * len(offsets(int(n3[0]))) + idx[0]
+                keys.append((slot, int(u[j, 0]), int(j)))
+            assert keys == sorted(keys)
