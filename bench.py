@@ -39,7 +39,7 @@ FORCE_KERNEL = "k_force<0, true, false>"  # RBL, FP32, no energy
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-full-list", action="store_true")
@@ -74,7 +74,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -124,7 +124,8 @@ def load_peaks():
 
 def load_traffic(N):
     """DRAM bytes per launch of the force kernel from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the current kernel source (else None).  The capture is of a smaller
+    system; traffic grows in proportion to N, so it is scaled per particle."""
     path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -209,9 +210,15 @@ def run_ours(a, rank, world, local):
     ms_graph, _ = timed(s, a.steps, phases=False)
     s.set_phase_timing(True)
 
-    # roofline of the force kernel (algorithmic bytes per particle)
+    # roofline of the force kernel: algorithmic bytes per particle of the data it must
+    # move -- own position 16, row counts and home cell 12, core row 4 n_c, the shell
+    # mask words of the home cell's stencil 4 ceil(M_c / 32), the home cell's segment
+    # table shared by the particles of the cell 16 S ncell / N, force out 24
     nc, p = obs["Nc_mean"], w["p"]
-    alg_bytes_pp = 16 + 4 + 4 * nc + 4 + 4 * p + 24
+    import math as _m
+    S = 25 if w["K"] == 2 else (2 * w["K"] + 1) ** 2
+    ncell = int(_m.floor(L[0] * w["K"] / (w["rs"] + w["skin"]))) ** 3
+    alg_bytes_pp = 16 + 12 + 4 * nc + 4 * _m.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24
     t_force = phase_ms[2] / nsteps * 1e-3
     achieved = alg_bytes_pp * N / t_force / 1e9
     peak, peak_kind = load_peaks()

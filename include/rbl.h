@@ -90,6 +90,7 @@ typedef struct {
     long long n_rebuild;  /* list builds so far */
     double Ns_mean;       /* mean shell (or full) row length at the last build */
     double Nc_mean;       /* mean core row length at the last build */
+    double Mc_mean;       /* mean stencil population of a particle's home cell at the last build */
     int Ns_max;           /* longest shell (or full) row at the last build */
     int Nc_max;           /* longest core row at the last build */
 } rbl_obs;

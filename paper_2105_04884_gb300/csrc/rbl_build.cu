@@ -31,6 +31,7 @@ __global__ void k_zero(View v, int conditional)
         v.sc->ns_max = 0;
         v.sc->ns_sum = 0ull;
         v.sc->nc_sum = 0ull;
+        v.sc->m_sum = 0ull;
         v.sc->m_max = 0;
     }
 }
@@ -149,9 +150,9 @@ __global__ void k_scatter(View v, int conditional)
     v.order[slot] = i;
 }
 
-// K2b: order every cell's members by tag: insertion sort on packed (tag, index)
-// keys, in registers/local memory for the usual small cells and in place in global
-// memory for larger ones (no occupancy limit).
+// K2b: order every cell's members by (x image, tag): insertion sort on packed
+// (u_x, tag) keys carrying the index, in local memory for the usual small cells
+// and in place in global memory for larger ones (no occupancy limit).
 __global__ void k_sort_cells(View v, int conditional)
 {
     if (skip(v, conditional)) return;
@@ -159,29 +160,37 @@ __global__ void k_sort_cells(View v, int conditional)
     if (c >= v.ncell) return;
     int s = v.start[c], e = v.start[c + 1];
     int m = e - s;
+    auto key_of = [&](int idx) -> unsigned long long {
+        int4 p = v.pos[idx];
+        return ((unsigned long long)(unsigned)p.x << 32) | (unsigned)p.w;
+    };
     if (m <= kCellCap) {
         unsigned long long key[kCellCap];
+        int val[kCellCap];
         for (int k = 0; k < m; ++k) {
-            int idx = v.order[s + k];
-            key[k] = ((unsigned long long)(unsigned)v.tag[idx] << 32) | (unsigned)idx;
+            val[k] = v.order[s + k];
+            key[k] = key_of(val[k]);
         }
         for (int a = 1; a < m; ++a) {
             unsigned long long x = key[a];
+            int xv = val[a];
             int b = a - 1;
             while (b >= 0 && key[b] > x) {
                 key[b + 1] = key[b];
+                val[b + 1] = val[b];
                 --b;
             }
             key[b + 1] = x;
+            val[b + 1] = xv;
         }
-        for (int k = 0; k < m; ++k) v.order[s + k] = (int)(unsigned)key[k];
+        for (int k = 0; k < m; ++k) v.order[s + k] = val[k];
     } else {
         int *o = v.order + s;
         for (int a = 1; a < m; ++a) {
             int x = o[a];
-            int tx = v.tag[x];
+            unsigned long long kx = key_of(x);
             int b = a - 1;
-            while (b >= 0 && v.tag[o[b]] > tx) {
+            while (b >= 0 && key_of(o[b]) > kx) {
                 o[b + 1] = o[b];
                 --b;
             }
@@ -243,6 +252,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
     __shared__ int s_pre[kBuildWarps][kMaxSeg + 1];
     __shared__ int s_a[kBuildWarps][kMaxSeg], s_la[kBuildWarps][kMaxSeg], s_b[kBuildWarps][kMaxSeg];
     __shared__ int4 s_pos[kBuildWarps][32];
+    __shared__ int s_j[kBuildWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * kBuildWarps + warp;
     if (c >= v.ncell) return; // whole warp; no block-wide barrier below
@@ -296,14 +306,14 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
     const int nchunk = (M + 31) >> 5;
     const bool full = v.full_list != 0;
     const size_t N = (size_t)v.N;
-    const unsigned lt = (1u << lane) - 1u;
     int wmc = 0, wms = 0;
     unsigned long long wsc = 0ull, wss = 0ull;
     for (int base = s0; base < s1; base += 32) {
         const int mm = min(32, s1 - base);
-        if (lane < mm) s_pos[warp][lane] = v.pos[base + lane];
+        const int i_me = base + lane; // the particle this lane stores for (lane < mm)
+        if (lane < mm) s_pos[warp][lane] = v.pos[i_me];
         __syncwarp();
-        int my_nc = 0, my_ns = 0; // counters of particle base + lane
+        int my_nc = 0, my_ns = 0;
         int seg = 0;
         for (int k = 0; k < nchunk; ++k) {
             const int cand = (k << 5) + lane;
@@ -314,10 +324,13 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
             const int j = off < lA[sg] ? sA[sg] + off : sB[sg] + (off - lA[sg]);
             const int4 pj = valid ? v.pos[j] : make_int4(0, 0, 0, 0);
             seg = __shfl_sync(0xffffffffu, sg, 31);
+            s_j[warp][lane] = j;
+            // test the 32 candidates against each particle of the pass; lane q keeps
+            // particle q's shell and core words
+            unsigned my_shell = 0u, my_core = 0u;
             for (int q = 0; q < mm; ++q) {
-                const int i = base + q;
                 PairGeom g = pair_geom(s_pos[warp][q], pj, v.h);
-                const bool other = valid && j != i;
+                const bool other = valid && j != base + q;
                 bool in_core, in_shell;
                 if (full) {
                     in_core = false;
@@ -327,22 +340,26 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
                     in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
                 }
                 const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
-                if (lane == 0) v.mask[(size_t)k * N + i] = bs;
-                if (lane == q) my_ns += __popc(bs);
                 const unsigned bc = __ballot_sync(0xffffffffu, in_core);
-                if (bc) {
-                    const int nc_q = __shfl_sync(0xffffffffu, my_nc, q);
-                    if (in_core) {
-                        int r = nc_q + __popc(bc & lt);
-                        if (r < v.cap_c) v.core[(size_t)r * N + i] = j;
-                    }
-                    if (lane == q) my_nc += __popc(bc);
+                my_shell = lane == q ? bs : my_shell;
+                my_core = lane == q ? bc : my_core;
+            }
+            __syncwarp();
+            if (lane < mm) {
+                v.mask[(size_t)k * N + i_me] = my_shell; // coalesced across lanes
+                my_ns += __popc(my_shell);
+                while (my_core) { // core row in candidate order
+                    const int b = __ffs(my_core) - 1;
+                    my_core &= my_core - 1u;
+                    if (my_nc < v.cap_c) v.core[(size_t)my_nc * N + i_me] = s_j[warp][b];
+                    ++my_nc;
                 }
             }
+            __syncwarp();
         }
         if (lane < mm) {
-            v.n_core[base + lane] = my_nc;
-            v.n_shell[base + lane] = my_ns;
+            v.n_core[i_me] = my_nc;
+            v.n_shell[i_me] = my_ns;
             if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
             wmc = max(wmc, my_nc);
             wms = max(wms, my_ns);
@@ -364,6 +381,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
         atomicMax(&v.sc->m_max, M);
         atomicAdd(&v.sc->nc_sum, wsc);
         atomicAdd(&v.sc->ns_sum, wss);
+        atomicAdd(&v.sc->m_sum, (unsigned long long)M * (unsigned long long)(s1 - s0));
     }
 }
 

@@ -351,6 +351,10 @@ rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t work
         v.inv[a] = 4294967296.0 / prm->L[a];
         v.h[a] = (float)(prm->L[a] / 4294967296.0);
     }
+    for (int sg = 0; sg < L.S; ++sg) {
+        v.seg_oz[sg] = (signed char)(sg / L.nofs3[1]);
+        v.seg_oy[sg] = (signed char)(sg % L.nofs3[1]);
+    }
     double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
     double lo = rc - sk > 0.0 ? rc - sk : 0.0;
     v.t_core_list = (float)((rc + sk) * (rc + sk));
@@ -552,6 +556,7 @@ rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out)
     out->n_rebuild = s.n_rebuild;
     out->Ns_mean = (double)s.ns_sum / v.N;
     out->Nc_mean = (double)s.nc_sum / v.N;
+    out->Mc_mean = (double)s.m_sum / v.N;
     out->Ns_max = s.ns_max;
     out->Nc_max = s.nc_max;
     return RBL_OK;
@@ -768,6 +773,10 @@ void static_view(View &v, const rbl_params *prm, int N, const Layout &L, char *b
         v.L[a] = prm->L[a];
         v.inv[a] = 4294967296.0 / prm->L[a];
         v.h[a] = (float)(prm->L[a] / 4294967296.0);
+    }
+    for (int sg = 0; sg < L.S; ++sg) {
+        v.seg_oz[sg] = (signed char)(sg / L.nofs3[1]);
+        v.seg_oy[sg] = (signed char)(sg % L.nofs3[1]);
     }
     double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
     double lo = rc - sk > 0.0 ? rc - sk : 0.0;

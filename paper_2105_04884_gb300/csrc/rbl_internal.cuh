@@ -36,6 +36,7 @@ struct DevScalars {
     int m_max;                      // largest stencil population at the last build
     unsigned long long ns_sum;      // total shell (or full) entries at the last build
     unsigned long long nc_sum;      // total core entries at the last build
+    unsigned long long m_sum;       // sum over particles of their home cell's stencil population
     long long n_rebuild;            // builds so far
     unsigned long long step;        // step counter n (batch/noise counters)
 };
@@ -59,6 +60,7 @@ struct DevScalars {
 struct View {
     int N, p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
     int ncell, n[3], nofs[3], ofs[3][kMaxStencil];
+    signed char seg_oy[kMaxStencil * kMaxStencil], seg_oz[kMaxStencil * kMaxStencil]; // row -> (oy, oz) slots
     double L[3], inv[3];            // inv = 2^32 / L
     float h[3];                     // L / 2^32 in binary32
     float t_core_list, t_shell_lo, t_cut_list, t_rc2, t_rs2, t_disp;
@@ -248,16 +250,22 @@ __device__ __forceinline__ int floyd_positions(unsigned long long seed, unsigned
     return p;
 }
 
-// Register-resident batch for p <= PMAX (a power of two): the Floyd positions,
-// sorted ascending and padded with INT_MAX; returns min(N_s, p).  Fast path: draw
-// q uses word q of the stream.  A draw whose low word lies below its bound could be
-// rejected by Lemire's rule and would shift the stream; the batch is then redrawn
-// by floyd_positions (the general sampler), so both paths give identical batches.
+// Register-resident batch for p <= PMAX: the Floyd positions, kept sorted ascending
+// while they are drawn and padded with INT_MAX; returns min(N_s, p).  Floyd's step q
+// either inserts t (uniform in [0, k]) or, when t is already taken, k itself -- and k
+// exceeds every earlier pick, so it lands at the end.  One pass of compares against
+// the sorted prefix gives both "already taken" and t's insertion point.
+// Fast path: draw q uses word q of the stream.  A draw whose low word lies below its
+// bound could be rejected by Lemire's rule and would shift the stream; the batch is
+// then redrawn by floyd_positions (the general sampler) and sorted, so both paths
+// give identical batches.
 template <int PMAX>
 __device__ __forceinline__ int batch_sorted(unsigned long long seed, unsigned long long step, int tag, int ns,
                                             int p, int (&S)[PMAX], unsigned *flags)
 {
     const int kInf = 0x7fffffff;
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) S[q] = kInf;
     if (ns <= p) {
 #pragma unroll
         for (int q = 0; q < PMAX; ++q) S[q] = q < ns ? q : kInf;
@@ -277,35 +285,33 @@ __device__ __forceinline__ int batch_sorted(unsigned long long seed, unsigned lo
             slow |= (uint32_t)m < bound;
             const int t = (int)(m >> 32);
             bool seen = false;
+            int pos = 0;
 #pragma unroll
-            for (int r = 0; r < q; ++r) seen |= (S[r] == t);
-            S[q] = seen ? (int)(bound - 1u) : t;
-        } else {
-            S[q] = kInf;
+            for (int r = 0; r < q; ++r) {
+                seen |= S[r] == t;
+                pos += S[r] < t ? 1 : 0;
+            }
+            const int x = seen ? (int)(bound - 1u) : t;
+            if (seen) pos = q;
+            // insert x at pos into the sorted prefix S[0..q)
+#pragma unroll
+            for (int r = q; r > 0; --r) S[r] = r > pos ? S[r - 1] : (r == pos ? x : S[r]);
+            S[0] = pos == 0 ? x : S[0];
         }
     }
     if (slow) {
         int T[kMaxP];
         const int nb = floyd_positions(seed, step, tag, ns, p, T, flags);
+        for (int a = 1; a < nb; ++a) { // insertion sort (rare path)
+            int x = T[a], b = a - 1;
+            while (b >= 0 && T[b] > x) {
+                T[b + 1] = T[b];
+                --b;
+            }
+            T[b + 1] = x;
+        }
 #pragma unroll
         for (int q = 0; q < PMAX; ++q) S[q] = q < nb ? T[q] : kInf;
-    }
-    // bitonic sort network on registers
-#pragma unroll
-    for (int k = 2; k <= PMAX; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-            for (int a = 0; a < PMAX; ++a) {
-                const int b = a ^ j;
-                if (b > a) {
-                    const int x = S[a], y = S[b];
-                    const bool up = (a & k) == 0;
-                    S[a] = up ? min(x, y) : max(x, y);
-                    S[b] = up ? max(x, y) : min(x, y);
-                }
-            }
-        }
     }
     return p;
 }

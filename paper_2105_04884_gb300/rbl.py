@@ -40,6 +40,7 @@ class rbl_obs(ctypes.Structure):
                 ("T_kin", ctypes.c_double), ("P", ctypes.c_double), ("U_tail", ctypes.c_double),
                 ("P_tail", ctypes.c_double), ("net_momentum", ctypes.c_double * 3), ("step", ctypes.c_longlong),
                 ("n_rebuild", ctypes.c_longlong), ("Ns_mean", ctypes.c_double), ("Nc_mean", ctypes.c_double),
+                ("Mc_mean", ctypes.c_double),
                 ("Ns_max", ctypes.c_int), ("Nc_max", ctypes.c_int)]
 
     def as_dict(self):
