@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--no-physics", action="store_true", help="skip the matched-physics block")
+    ap.add_argument("--physics", action="store_true",
+                    help="run the full matched-physics sweep (r_c x p x precision vs the full list) instead")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="override particle count (debug only)")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
@@ -137,6 +140,151 @@ def load_traffic(N):
         return float(d["dram_bytes_per_particle"]) * N
     except Exception:
         return None
+
+
+# Matched-physics study: LJ fluid N = 32,000 (FCC 20^3 x 4), rho* = 0.8442, T* = 1.2,
+# Langevin gamma = 1, dt = 0.005, r_s = 3.5, skin 0.3; 10^4 steps, the first 2000
+# discarded, block averages over blocks of 500 steps.
+PHYS = dict(N=32000, rho=0.8442, T=1.2, rs=3.5, skin=0.3, dt=0.005, gamma=1.0, K=2, steps=10000, discard=2000,
+            block=500, stride=10, rdf_every=5, dr=0.02)
+
+
+def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS):
+    """Block-averaged observables of one NVT trajectory.  Pressure and energy are the
+    exact (unsampled) ones of the configurations the dynamics visits: P = rho T_kin +
+    W / (3V) and U / N with W, U over every pair with r < r_s; the RBL estimates of the
+    same quantities are reported beside them.  g(r) from ordered-pair counts."""
+    import numpy as np
+
+    from paper_2105_04884_gb300 import rbl
+
+    N = len(x)
+    V = float(np.prod(L))
+    rho = N / V
+    s = rbl.System(x, v, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
+                   gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision, full_list=full)
+    nbins = int(round(cfg["rs"] / cfg["dr"]))
+    s.step(cfg["discard"])
+    nblk = (cfg["steps"] - cfg["discard"]) // cfg["block"]
+    per = cfg["block"] // cfg["stride"]
+    blocks = {k: [] for k in ("P", "P_bath", "U", "T", "P_est", "U_est")}
+    g_blocks = []
+    shell = 4.0 / 3.0 * math.pi * (np.arange(1, nbins + 1) ** 3 - np.arange(nbins) ** 3) * cfg["dr"] ** 3
+    t0 = time.perf_counter()
+    for _ in range(nblk):
+        acc = {k: 0.0 for k in blocks}
+        h = np.zeros(nbins, np.int64)
+        nr = 0
+        for k in range(per):
+            s.step(cfg["stride"])
+            U, W = s.exact_energy()
+            o = s.observables()
+            acc["P"] += rho * o["T_kin"] + W / (3 * V)
+            acc["P_bath"] += rho * cfg["T"] + W / (3 * V)  # Sec. 3: rho / beta + virial
+            acc["U"] += U / N
+            acc["T"] += o["T_kin"]
+            acc["P_est"] += rho * o["T_kin"] + o["W_est"] / (3 * V)
+            acc["U_est"] += o["U_est"] / N
+            if (k + 1) % cfg["rdf_every"] == 0:
+                s.rdf(cfg["dr"], nbins, h)
+                nr += 1
+        for k in blocks:
+            blocks[k].append(acc[k] / per)
+        g_blocks.append(h / (nr * N * rho * shell))
+    wall = time.perf_counter() - t0
+    heating = None
+    if not full:
+        # numerical heating check: the per-particle variance of the RBL force error
+        # chi = F_rbl - F_exact at the final configuration predicts, for BAOAB with
+        # friction gamma, a kinetic temperature excess dT = dt <|chi|^2> / (6 gamma)
+        xs, vs, _ = s.get_state()
+        F_rbl = s.forces()
+        ref = rbl.System(xs, vs, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
+                         gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision,
+                         full_list=True)
+        F_ex = ref.forces()
+        var = float(np.mean(np.sum((F_rbl - F_ex) ** 2, axis=1)))
+        heating = {"force_err_var": var, "dT_predicted": cfg["dt"] * var / (6.0 * cfg["gamma"])}
+        del ref
+    out = {"heating": heating}
+    for k, b in blocks.items():
+        b = np.asarray(b)
+        out[k] = [float(b.mean()), float(b.std(ddof=1) / math.sqrt(len(b)))]
+    g = np.asarray(g_blocks)
+    out["g"] = g.mean(0)
+    out["g_err"] = g.std(0, ddof=1) / math.sqrt(len(g))
+    out["wall_s"] = wall
+    out["n_rebuild"] = s.observables()["n_rebuild"]
+    return out
+
+
+def physics_compare(a, b, dr):
+    """z-scores of the scalar differences (combined block-average errors) and the
+    reduced chi^2 of the g(r) difference over bins where g > 0.05."""
+    import numpy as np
+
+    res = {}
+    for k in ("P", "P_bath", "U", "T"):
+        d = a[k][0] - b[k][0]
+        e = math.hypot(a[k][1], b[k][1])
+        res[k] = {"rbl": a[k], "full": b[k], "z": d / e if e > 0 else None}
+    m = (a["g"] > 0.05) | (b["g"] > 0.05)
+    var = a["g_err"][m] ** 2 + b["g_err"][m] ** 2
+    ok = var > 0
+    chi2 = float(np.mean((a["g"][m][ok] - b["g"][m][ok]) ** 2 / var[ok]))
+    ia, ib = int(np.argmax(a["g"])), int(np.argmax(b["g"]))
+    res["g"] = {"chi2_per_bin": chi2, "bins": int(ok.sum()), "dr": dr,
+                "peak_rbl": [float(a["g"][ia]), float(a["g_err"][ia]), (ia + 0.5) * dr],
+                "peak_full": [float(b["g"][ib]), float(b["g_err"][ib]), (ib + 0.5) * dr],
+                "max_abs_diff": float(np.max(np.abs(a["g"] - b["g"])))}
+    return res
+
+
+def physics_inputs(seed=1, cfg=PHYS):
+    from paper_2105_04884_gb300 import inputs
+
+    x, L = inputs.fcc(cfg["N"], cfg["rho"], 0.01, seed=seed)
+    v = inputs.maxwell_boltzmann(cfg["N"], cfg["T"], seed=seed)
+    return x, v, L
+
+
+def matched_physics_pair(rc=1.5, p=10, cfg=PHYS, full=None):
+    """RBL (FP32, r_c, p) against the full list (FP32) on the same start."""
+    from paper_2105_04884_gb300 import rbl
+
+    x, v, L = physics_inputs(cfg=cfg)
+    a = physics_run(x, v, L, rc, p, rbl.RBL_FP32, False, 1, cfg)
+    b = full if full is not None else physics_run(x, v, L, rc, p, rbl.RBL_FP32, True, 1, cfg)
+    res = physics_compare(a, b, cfg["dr"])
+    res["workload"] = "lj_fluid_N32000_rho0.8442_T1.2_rs3.5_nvt"
+    res["r_c"], res["p"] = rc, p
+    res["steps"], res["discard"], res["block"] = cfg["steps"], cfg["discard"], cfg["block"]
+    res["P_est_rbl"] = a["P_est"]
+    res["U_est_rbl"] = a["U_est"]
+    if a["heating"]:
+        res["heating"] = dict(a["heating"], dT_measured=a["T"][0] - b["T"][0])
+    res["wall_s"] = a["wall_s"] + b["wall_s"]
+    return res, b
+
+
+def physics_sweep():
+    """The full study: r_c in {1.2, 1.5, 2.0} x p in {1, 2, 5, 10, 20}, FP32 and FP64,
+    each against the full list of the same precision.  One JSON line per run."""
+    from paper_2105_04884_gb300 import rbl
+
+    x, v, L = physics_inputs()
+    for prec, name in ((rbl.RBL_FP32, "fp32"), (rbl.RBL_FP64, "fp64")):
+        ref = physics_run(x, v, L, 1.5, 10, prec, True, 1)
+        print(json.dumps({"precision": name, "method": "full", "P": ref["P"], "U": ref["U"], "T": ref["T"],
+                          "wall_s": ref["wall_s"]}), flush=True)
+        for rc in (1.2, 1.5, 2.0):
+            for p in (1, 2, 5, 10, 20):
+                r = physics_run(x, v, L, rc, p, prec, False, 1)
+                c = physics_compare(r, ref, PHYS["dr"])
+                c.update({"precision": name, "method": "rbl", "r_c": rc, "p": p, "P_est": r["P_est"],
+                          "U_est": r["U_est"], "wall_s": r["wall_s"], "n_rebuild": r["n_rebuild"],
+                          "heating": dict(r["heating"], dT_measured=r["T"][0] - ref["T"][0])})
+                print(json.dumps(c), flush=True)
 
 
 def make_workload(N, seed):
@@ -259,6 +407,16 @@ def run_ours(a, rank, world, local):
         result["speedup_vs_full_list"] = value / vf
         del sf
         torch.cuda.empty_cache()
+        # the same workload at r_c = 2.0 (where the block-averaged P, U and g(r) of the
+        # RBL trajectory match the full list's; see "matched_physics")
+        s2 = rbl.System(x, v, L, **dict(common, r_c=2.0))
+        s2.step(a.warmup)
+        ms2, (pm2, n2) = timed(s2, a.steps, phases=True)
+        v2 = N * a.steps * world / (ms2 * 1e-3)
+        result["rbl_rc2.0"] = {"value": v2, "ms_per_step": ms2 / a.steps, "force_kernel_ms": pm2[2] / n2,
+                               "speedup_vs_full_list": v2 / vf}
+        del s2
+        torch.cuda.empty_cache()
     # end to end through the C ABI with host buffers: upload once, K x (step + scalar
     # readback), download the final state
     if not a.no_e2e:
@@ -290,6 +448,12 @@ def run_ours(a, rank, world, local):
                          "d2h_bytes_per_step": 48 * N / a.steps + 256,
                          "path": "rbl_set_state(host) + steps x (rbl_step(1) + rbl_observables) + rbl_get_state(host)"}
         del se
+    if rank == 0 and not a.no_physics:
+        # the bench workload's (r_c, p) and r_c = 2.0 (the matched setting), each
+        # against one full-list trajectory
+        mp, full_run = matched_physics_pair(1.5, 10)
+        mp2, _ = matched_physics_pair(2.0, 10, full=full_run)
+        result["matched_physics"] = [mp, mp2]
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(x, v, L, a.cpu_steps)
     if world > 1:
@@ -299,53 +463,75 @@ def run_ours(a, rank, world, local):
     return result
 
 
-def cpu_baseline(x, v, L, steps):
+def cpu_baseline(x, v, L, steps, steps_single=3):
+    """The oracle timed on the host cores: OpenMP over every core, and single-threaded
+    (the paper's own setting, one core).  Each sample starts from the workload's
+    initial state, so it includes one list build."""
     import oracle
 
     w = WORKLOAD
     cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    args = (L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1)
+    oracle.set_threads(cores)
     t0 = time.perf_counter()
-    oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, steps)
+    oracle.run(x, v, *args, steps)
     t = time.perf_counter() - t0
-    return {"value": len(x) * steps / t, "unit": "particle-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle",
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.run(x, v, *args, steps_single)
+    t1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    return {"value": len(x) * steps / t, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{steps} steps of the same N={len(x)} workload from its start (includes the initial list "
-                      f"build), FP64 C oracle with OpenMP"}
+                      f"build), FP64 C oracle with OpenMP on {cores} threads",
+            "single_thread": {"value": len(x) * steps_single / t1, "unit": "particle-steps/s", "cores": 1,
+                              "sample": f"{steps_single} steps of the same workload from its start, 1 thread"}}
+
+
+REF_BUDGET_S = 120.0  # timed oracle work of the reference arm
 
 
 def run_reference(a, rank, world):
+    """The oracle as the reference arm: warm-up steps, then as many of the requested
+    timed steps as fit in REF_BUDGET_S (estimated from the warm-up), on every host
+    core.  Ranks other than 0 exit without work."""
     if rank != 0:
         return None
-    import numpy as np  # noqa: F401
-
     import oracle
 
     w = WORKLOAD
     N = a.N
     x, v, L = make_workload(N, 1)
     cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     oracle.build()
-    x, v, _, _ = oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, a.warmup)
+    oracle.set_threads(cores)
+    args = (L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1)
+    tw = time.perf_counter()
+    x, v, _, _ = oracle.run(x, v, *args, a.warmup)
+    tw = (time.perf_counter() - tw) / a.warmup
+    k = max(1, min(a.steps, int(REF_BUDGET_S / max(tw, 1e-9))))
     t0 = time.perf_counter()
-    oracle.run(x, v, L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1, a.steps,
-               step0=a.warmup)
+    oracle.run(x, v, *args, k, step0=a.warmup)
     t = time.perf_counter() - t0
-    value = N * a.steps / t
+    value = N * k / t
+    sample = (f"{k} of the {a.steps} requested steps of the full N={N} workload after {a.warmup} warm-up steps "
+              f"(lists rebuilt at the start of the timed call), bounded to ~{REF_BUDGET_S:.0f} s of CPU time")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3 / a.steps, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3 / k, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "N": N},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
-                             "kind": "oracle", "sample": f"{a.steps} timed steps of the full workload (lists "
-                                                         f"rebuilt at the start of the timed call)"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     a = parse()
     rank, world, local = dist_info()
+    if a.physics:
+        if rank == 0:
+            physics_sweep()
+        return
     if a.impl == "reference":
         res = run_reference(a, rank, world)
     else:

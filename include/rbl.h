@@ -140,9 +140,20 @@ rbl_status rbl_step(rbl_ctx *ctx, int n);
  * and virial from the last force evaluation).  Synchronises. */
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
 
+/* The energy and virial of the truncated potential at the current positions, with
+ * no sampling: *U = sum over pairs i<j with r_ij < r_s of u(r_ij), *W the virial
+ * sum r.f over the same pairs (Sec. 3 observables; the quantities the RBL estimates
+ * U_est, W_est are unbiased for).  Every core entry with r < r_c and every shell
+ * entry with r_c <= r < r_s is summed once per ordered pair and halved, so the cost
+ * is that of a full-list force pass; nothing in the context's force state changes.
+ * Pair terms in the context's precision, per-particle sums then FP64.  Builds lists
+ * if stale.  Synchronises; host pointers. */
+rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W);
+
 /* Parity hooks.  kind 0 = core rows, 1 = shell rows (full rows when full_list).
  * rows[N][cap] receives neighbour TAGS in the canonical row order (stencil slot of
- * the neighbour's cell, then tag), counts[N] the lengths; host pointers.  Rows
+ * the neighbour's cell, then the neighbour's 32-bit x image, then tag), counts[N]
+ * the lengths; host pointers.  Rows
  * longer than cap return RBL_EOVERFLOW. Builds lists if stale. */
 rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts);
 

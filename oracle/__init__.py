@@ -55,6 +55,10 @@ F = ctypes.c_float
 
 
 def _declare(L):
+    L.orc_set_threads.argtypes = [I]
+    L.orc_set_threads.restype = None
+    L.orc_max_threads.argtypes = []
+    L.orc_max_threads.restype = I
     L.orc_philox4x32_10.argtypes = [P, P, P]
     L.orc_stream_words.argtypes = [U64, U64, U32, U32, I, P]
     L.orc_stream_uniform_below.argtypes = [U64, U64, U32, U32, U32, I, P]
@@ -247,6 +251,15 @@ def subtract_mean(F):
     F = _f64(F, (-1, 3)).copy()
     lib().orc_subtract_mean(F.shape[0], _p(F))
     return F
+
+
+def set_threads(n):
+    """OpenMP threads for the oracle's loops (timing only)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads():
+    return int(lib().orc_max_threads())
 
 
 def run(x, v, L, rc, rs, skin, p, dt, T, gamma, seed, n_steps, step0=0, K=2, subtract_mean=True,

@@ -919,3 +919,26 @@ void orc_rdf_counts(int n, const double *x, const double L[3], float dr, int nbi
         }
     free(u);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Thread count of the OpenMP loops, for timing the oracle single-threaded and on
+ * all host cores.  Forces, lists and trajectories do not depend on it; only the
+ * order of the FP64 energy/virial reductions does.                           */
+/* ------------------------------------------------------------------------- */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

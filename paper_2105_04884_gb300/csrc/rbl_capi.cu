@@ -562,6 +562,19 @@ rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out)
     return RBL_OK;
 }
 
+rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W)
+{
+    if (!ctx || !U || !W) return RBL_EINVAL;
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    CK(launch_exact_energy(ctx->view, ctx->stream));
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    *U = ctx->h_sc->u_exact;
+    *W = ctx->h_sc->w_exact;
+    return RBL_OK;
+}
+
 rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts)
 {
     if (!ctx || !rows || !counts || (kind != 0 && kind != 1) || cap < 1) return RBL_EINVAL;

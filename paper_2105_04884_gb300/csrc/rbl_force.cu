@@ -139,7 +139,9 @@ __device__ __forceinline__ void sort_small(int *S, int n)
     }
 }
 
-// MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (mask).
+// MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (mask);
+// MODE 2: exact observables -- the core list and every shell (or full) mask entry,
+// unsampled, energy and virial only (no force written, no total force).
 // PMAX > 0: batch positions and neighbour indices live in registers (p <= PMAX);
 // PMAX = 0: general path through local arrays (p up to kMaxP).
 //
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
     double e_i = 0.0, w_i = 0.0;
     if (i < v.N) {
         const int4 pi = v.pos[i];
-        const int nc = MODE == 0 ? min(v.n_core[i], v.cap_c) : 0;
+        const int nc = (MODE == 0 || (MODE == 2 && !v.full_list)) ? min(v.n_core[i], v.cap_c) : 0;
         const int ns = v.n_shell[i];
         const int4 *tab = v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S;
         const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
@@ -253,18 +255,19 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                     acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
                 }
             }
-            // core row, kGather at a time
-            for (int k0 = 0; k0 < nc; k0 += kGather) {
-                int jj[kGather];
+        }
+        // core row, kGather at a time
+        for (int k0 = 0; k0 < nc; k0 += kGather) {
+            int jj[kGather];
 #pragma unroll
-                for (int u = 0; u < kGather; ++u) {
-                    const int k = k0 + u;
-                    jj[u] = k < nc ? v.core[(size_t)k * N + i] : i;
-                }
-                acc.template pairs<kGather>(v, pi, i, jj, nc - k0, 0);
+            for (int u = 0; u < kGather; ++u) {
+                const int k = k0 + u;
+                jj[u] = k < nc ? v.core[(size_t)k * N + i] : i;
             }
-        } else {
-            // full list: walk the mask, kGather members at a time
+            acc.template pairs<kGather>(v, pi, i, jj, nc - k0, 0);
+        }
+        if (MODE != 0) {
+            // every mask entry, kGather members at a time
             int w = 0;
             unsigned word = ns > 0 ? mask_word(0) : 0u;
             for (int k0 = 0; k0 < ns; k0 += kGather) {
@@ -282,7 +285,15 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                 acc.template pairs<kGather>(v, pi, i, jj, ns - k0, 1);
             }
         }
-        if (FP32) {
+        if (MODE == 2) {
+            if (FP32) {
+                e_i = 0.5 * ((double)acc.e32[0] + (double)acc.e32[1]);
+                w_i = 0.5 * ((double)acc.w32[0] + (double)acc.w32[1]);
+            } else {
+                e_i = 0.5 * (acc.e64[0] + acc.e64[1]);
+                w_i = 0.5 * (acc.w64[0] + acc.w64[1]);
+            }
+        } else if (FP32) {
             long long *F = (long long *)v.F;
             FixedAcc fx;
             fx.zero();
@@ -311,7 +322,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
         }
     }
     // Total force and energy/virial partials.
-    if (FP32) {
+    if (MODE == 2) {
+        double x[2] = {e_i, w_i};
+        block_sum_d<2, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8 + 3);
+    } else if (FP32) {
         int lane = threadIdx.x & 31;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -330,8 +344,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
 
 // Reduce the block partials in a fixed order; form the mean force F_cor
 // (Appendix A) and reset the integer accumulator for the next evaluation.
+// exact = 1: store the unsampled energy and virial only (MODE 2 partials).
 __global__ void __launch_bounds__(1024) k_force_finish(View v, int nblk, int fp32, int energy, int subtract,
-                                                       int advance)
+                                                       int advance, int exact)
 {
     __shared__ double sh[5][32];
     double acc[5] = {0, 0, 0, 0, 0};
@@ -351,6 +366,11 @@ __global__ void __launch_bounds__(1024) k_force_finish(View v, int nblk, int fp3
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int k = 0; k < 5; ++k) tot[k] += sh[k][w];
         DevScalars *sc = v.sc;
+        if (exact) {
+            sc->u_exact = tot[3];
+            sc->w_exact = tot[4];
+            return;
+        }
         for (int a = 0; a < 3; ++a) {
             double m;
             if (fp32) {
@@ -478,7 +498,16 @@ cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStr
     int g = ceil_div(v.N, kForceThreads);
     bool fp32 = v.precision == RBL_FP32;
     int threads = (fp32 && !energy) ? 32 : 1024;
-    k_force_finish<<<1, threads, 0, s>>>(v, g, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance);
+    k_force_finish<<<1, threads, 0, s>>>(v, g, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_energy(const View &v, cudaStream_t s)
+{
+    int g = ceil_div(v.N, kForceThreads);
+    if (v.precision == RBL_FP32) k_force<2, true, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
+    else k_force<2, false, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
+    k_force_finish<<<1, 1024, 0, s>>>(v, g, 0, 1, 0, 0, 1);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ struct DevScalars {
     unsigned long long fsum_q[3];   // FP32 path: sum of fixed-point forces (mod 2^64)
     double fcor[3];                 // mean force subtracted from every particle
     double energy, virial;          // RBL estimates from the last evaluation
+    double u_exact, w_exact;        // unsampled energy and virial (on demand)
     double ksum;                    // sum v^2 (on demand)
     double psum[3];                 // sum v (on demand)
     unsigned flags;                 // kFlag* bits
@@ -507,6 +508,7 @@ cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHand
 cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
 cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s);
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s);
+cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
 cudaError_t launch_kinetic(const View &v, cudaStream_t s);

@@ -50,7 +50,8 @@ class rbl_obs(ctypes.Structure):
 
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_create", "rbl_set_state", "rbl_get_state",
-           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_get_lists", "rbl_get_batch",
+           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists",
+           "rbl_get_batch",
            "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_forces_static", "rbl_destroy",
            "rbl_last_error", "rbl_status_string"]
 
@@ -223,6 +224,13 @@ class System:
         o = rbl_obs()
         self._check(self.lib.rbl_observables(self.h, ctypes.byref(o)))
         return o.as_dict()
+
+    def exact_energy(self):
+        """(U, W): unsampled energy and virial sums over all pairs with r < r_s."""
+        U = ctypes.c_double()
+        W = ctypes.c_double()
+        self._check(self.lib.rbl_exact_energy(self.h, ctypes.byref(U), ctypes.byref(W)))
+        return U.value, W.value
 
     def get_lists(self, kind, cap=None):
         if cap is None:

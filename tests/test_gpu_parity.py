@@ -117,6 +117,26 @@ def test_full_list_forces(case, precision, tol):
     assert abs(obs["U_est"] - ev[0]) <= tol * abs(ev[0]) * 10
 
 
+@pytest.mark.parametrize("full", [False, True])
+@pytest.mark.parametrize("precision,tol", [(rbl.RBL_FP64, 1e-12), (rbl.RBL_FP32, 1e-5)])
+def test_exact_energy(case, precision, tol, full):
+    """The unsampled energy and virial (every pair with r < r_s, from the core and
+    shell lists, or the full list) equal the oracle's full-list sums; the call leaves
+    the force state and the RBL estimates untouched."""
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L, precision=precision, full_list=full)
+    F0 = s.forces()
+    est0 = s.observables()
+    U, W = s.exact_energy()
+    _, ev = oracle.full_forces(x, L, c["rs"], lists)
+    # FP32: per-pair binary32 terms summed in binary32 per particle (~200 terms)
+    assert abs(U - ev[0]) <= tol * abs(ev[0]) * 10
+    assert abs(W - ev[1]) <= tol * abs(ev[1]) * 10
+    est1 = s.observables()
+    assert est1["U_est"] == est0["U_est"] and est1["W_est"] == est0["W_est"]
+    assert np.array_equal(s.forces(), F0)
+
+
 @pytest.mark.parametrize("N,rho,seed", [(1000, 0.8, 11), (2501, 0.9, 12), (800, 0.6, 13)])
 def test_fp32_large_batch_is_full_list(N, rho, seed):
     """p >= max N_s takes every shell neighbour with scale 1, so the RBL force equals
