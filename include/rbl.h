@@ -14,6 +14,12 @@
  *  - Particle arrays passed in or out are in TAG order (row t describes the particle
  *    whose tag is t), AoS [N][3] doubles for positions/velocities/forces.  Inside the
  *    context particles are kept in cell order; the library translates.
+ *  - Replicas: a context holds R >= 1 independent systems (rbl_create: R = 1;
+ *    rbl_create_batch: any R), advanced together by one launch per kernel.  Per-
+ *    particle arrays then hold the replicas' rows one after another ("packed": rows
+ *    in0_r .. in0_r + N_r - 1 for replica r, in0_r = N_0 + ... + N_{r-1}); tags and
+ *    neighbour tags are numbers within a replica.  Per-replica outputs (rbl_obs,
+ *    exact energies, histograms) are arrays of R.
  *  - "ptr_is_device": 0 means the pointer is host memory (the call copies through
  *    the context's stream and synchronises), 1 means device memory on the context's
  *    device (the call is asynchronous on the context's stream).
@@ -110,6 +116,23 @@ rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes);
 rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,
                       rbl_ctx **out);
 
+/* Batched ensemble: R independent replicas of N[r] particles each, with parameters
+ * prm[r] (each validated as for rbl_create).  Replicas may differ in the box L, the
+ * bath temperature T, the seed and N; every other field must equal prm[0]'s
+ * (RBL_EINVAL otherwise).  Each replica evolves exactly as a context of its own
+ * would: its own Philox streams (its seed, its tags), its own net-force correction,
+ * and its own rebuild decisions (a replica's lists are rebuilt only when one of its
+ * own particles moved more than skin/2).  Every kernel launch covers all replicas,
+ * and the steady-state step is one CUDA graph for the whole ensemble.  Particle
+ * slots are allocated per replica in multiples of 256, so a workspace for R small
+ * replicas is larger than one for a single system of the same total N. */
+rbl_status rbl_workspace_size_batch(const rbl_params *prm, int R, const int *N, size_t *bytes);
+rbl_status rbl_create_batch(const rbl_params *prm, int R, const int *N, void *workspace, size_t workspace_bytes,
+                            void *stream, rbl_ctx **out);
+
+/* Number of replicas of a context (0 for NULL). */
+int rbl_replicas(const rbl_ctx *ctx);
+
 /* Loads positions x[N][3] (wrapped into [0, L)), velocities v[N][3] (may be NULL:
  * zero) and the step counter; marks the lists stale.  Rejects non-finite input. */
 rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long long step, int ptr_is_device);
@@ -137,7 +160,8 @@ rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device);
 rbl_status rbl_step(rbl_ctx *ctx, int n);
 
 /* Scalars of the current state (kinetic terms from the current velocities, energy
- * and virial from the last force evaluation).  Synchronises. */
+ * and virial from the last force evaluation), out[R]: one per replica.
+ * Synchronises. */
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
 
 /* The energy and virial of the truncated potential at the current positions, with
@@ -147,7 +171,7 @@ rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
  * entry with r_c <= r < r_s is summed once per ordered pair and halved, so the cost
  * is that of a full-list force pass; nothing in the context's force state changes.
  * Pair terms in the context's precision, per-particle sums then FP64.  Builds lists
- * if stale.  Synchronises; host pointers. */
+ * if stale.  U[R], W[R]: one per replica.  Synchronises; host pointers. */
 rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W);
 
 /* Parity hooks.  kind 0 = core rows, 1 = shell rows (full rows when full_list).
@@ -166,8 +190,8 @@ rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts);
  * pairs i != j with r < r_s and floor(sqrt(r2) / dr) = b < nbins, each pair taken
  * from the list that classifies it like the force does (core rows for r < r_c,
  * shell rows for r_c <= r < r_s; full rows in full-list mode).  Requires
- * nbins * dr <= r_s.  hist[nbins] int64, host pointer, accumulated (not cleared).
- * Builds lists if stale. */
+ * nbins * dr <= r_s.  hist[R][nbins] int64 (one histogram per replica), host
+ * pointer, accumulated (not cleared).  Builds lists if stale. */
 rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
 
 /* Phase timing.  While enabled, rbl_step launches each step's phases directly (no

@@ -1,38 +1,63 @@
 // rbl_build.cu -- linked cells and two-level neighbour lists (Sec. 2, Fig. 1).
 //
 // A rebuild is: cell hash + occupancy count (K1), exclusive scan of the counts,
-// scatter into cell order and a per-cell sort by tag (K2), permutation of the
-// particle state into that order, and the list build (K3).  Every kernel takes a
-// `conditional` flag: in the stepping loop the rebuild is enqueued every step and
-// each kernel returns at once unless the integrator raised the device flag
-// DevScalars::rebuild, so no host round trip decides whether to rebuild.
+// scatter into cell order and a per-cell sort by (x image, tag) (K2), permutation
+// of the particle state into that order, and the list build (K3).  One launch per
+// kernel covers every replica of the context.  Every kernel takes a `conditional`
+// flag: in the stepping loop the chain runs only when the integrator raised some
+// replica's device flag, and then each kernel leaves the particles and cells of
+// replicas whose own flag is down untouched (their counts, order and lists stay
+// valid, and the one scan over all cells reproduces their starts), so replicas
+// rebuild exactly when they would on their own.
 #include "rbl_internal.cuh"
 
 namespace rbl {
 
 namespace {
 
+// Whole-kernel early exit: no replica is due.
 __device__ __forceinline__ bool skip(const View &v, int conditional)
 {
     return conditional && v.sc->rebuild == 0;
 }
 
-// Zero the occupancy counters and the build statistics.
+// Replica r takes part in this rebuild.
+__device__ __forceinline__ bool active(const View &v, int conditional, int r)
+{
+    return !conditional || v.rs[r].rebuild != 0;
+}
+
+// Particle slot i that holds a particle of a rebuilding replica; r its replica.
+__device__ __forceinline__ bool active_slot(const View &v, int conditional, int i, int &r)
+{
+    if (i >= v.N) return false;
+    bool live;
+    r = slot_replica(v, i, live);
+    return live && active(v, conditional, r);
+}
+
+// Zero the occupancy counters (the pad cell of a replica holds its padding slots)
+// and the build statistics of the rebuilding replicas.
 __global__ void k_zero(View v, int conditional)
 {
     if (skip(v, conditional)) return;
     int stride = gridDim.x * blockDim.x;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.ncell; c += stride) {
-        v.counts[c] = 0;
+        const int r = v.cell_rep[c];
+        if (!active(v, conditional, r)) continue;
+        const Box &b = v.box[r];
+        v.counts[c] = c == b.c0 + b.ncell ? b.slots - b.N : 0;
         v.fill[c] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        v.sc->nc_max = 0;
-        v.sc->ns_max = 0;
-        v.sc->ns_sum = 0ull;
-        v.sc->nc_sum = 0ull;
-        v.sc->m_sum = 0ull;
-        v.sc->m_max = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < v.R; r += stride) {
+        if (!active(v, conditional, r)) continue;
+        RepScalars &q = v.rs[r];
+        q.nc_max = 0;
+        q.ns_max = 0;
+        q.m_max = 0;
+        q.ns_sum = 0ull;
+        q.nc_sum = 0ull;
+        q.m_sum = 0ull;
     }
 }
 
@@ -40,13 +65,14 @@ __global__ void k_zero(View v, int conditional)
 __global__ void k_cell_hash(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.N) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x, r;
+    if (!active_slot(v, conditional, i, r)) return;
+    const Box &b = v.box[r];
     int4 p = v.pos[i];
-    int cx = cell_coord((unsigned)p.x, v.n[0]);
-    int cy = cell_coord((unsigned)p.y, v.n[1]);
-    int cz = cell_coord((unsigned)p.z, v.n[2]);
-    int c = (cz * v.n[1] + cy) * v.n[0] + cx;
+    int cx = cell_coord((unsigned)p.x, b.n[0]);
+    int cy = cell_coord((unsigned)p.y, b.n[1]);
+    int cz = cell_coord((unsigned)p.z, b.n[2]);
+    int c = b.c0 + (cz * b.n[1] + cy) * b.n[0] + cx;
     v.cell[i] = c;
     atomicAdd(&v.counts[c], 1);
 }
@@ -143,8 +169,8 @@ __global__ void k_scan_add(View v, int conditional)
 __global__ void k_scatter(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.N) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x, r;
+    if (!active_slot(v, conditional, i, r)) return;
     int c = v.cell[i];
     int slot = v.start[c] + atomicAdd(&v.fill[c], 1);
     v.order[slot] = i;
@@ -158,6 +184,8 @@ __global__ void k_sort_cells(View v, int conditional)
     if (skip(v, conditional)) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= v.ncell) return;
+    const int r = v.cell_rep[c];
+    if (!active(v, conditional, r) || c == v.box[r].c0 + v.box[r].ncell) return; // pad cell: no particles
     int s = v.start[c], e = v.start[c + 1];
     int m = e - s;
     auto key_of = [&](int idx) -> unsigned long long {
@@ -203,8 +231,8 @@ __global__ void k_sort_cells(View v, int conditional)
 __global__ void k_permute(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= v.N) return;
+    int k = blockIdx.x * blockDim.x + threadIdx.x, r;
+    if (!active_slot(v, conditional, k, r)) return;
     int old = v.order[k];
     size_t N = (size_t)v.N;
 #pragma unroll
@@ -220,8 +248,8 @@ __global__ void k_permute(View v, int conditional)
 __global__ void k_copy_back(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= v.N) return;
+    int k = blockIdx.x * blockDim.x + threadIdx.x, r;
+    if (!active_slot(v, conditional, k, r)) return;
     size_t N = (size_t)v.N;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -244,7 +272,6 @@ __global__ void k_copy_back(View v, int conditional)
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
 // k.  Row lengths are counted past the core capacity.
 constexpr int kBuildWarps = 4;
-constexpr int kMaxSeg = kMaxStencil * kMaxStencil;
 
 __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int conditional)
 {
@@ -256,21 +283,27 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * kBuildWarps + warp;
     if (c >= v.ncell) return; // whole warp; no block-wide barrier below
+    const int r = v.cell_rep[c];
+    const Box &b = v.box[r];
+    const int lc = c - b.c0;
+    if (lc == b.ncell || !active(v, conditional, r)) return; // pad cell, or not rebuilding
     int *pre = s_pre[warp], *sA = s_a[warp], *lA = s_la[warp], *sB = s_b[warp];
-    const int cx = c % v.n[0], cy = (c / v.n[0]) % v.n[1], cz = c / (v.n[0] * v.n[1]);
-    const int S = v.S;
+    const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
+    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+    const int S = b.S;
+    const int nofs0 = b.nofs[0], nofs1 = b.nofs[1];
     for (int sg = lane; sg < S; sg += 32) {
-        int oz = sg / v.nofs[1], oy = sg - oz * v.nofs[1];
-        int czz = wrap_cell(cz + v.ofs[2][oz], v.n[2]);
-        int cyy = wrap_cell(cy + v.ofs[1][oy], v.n[1]);
-        int rowbase = (czz * v.n[1] + cyy) * v.n[0];
-        int fx = wrap_cell(cx + v.ofs[0][0], v.n[0]);
-        int last = fx + v.nofs[0] - 1;
-        int lastA = last < v.n[0] ? last : v.n[0] - 1;
+        int oz = sg / nofs1, oy = sg - oz * nofs1;
+        int czz = wrap_cell(cz + b.ofs[2][oz], n2);
+        int cyy = wrap_cell(cy + b.ofs[1][oy], n1);
+        int rowbase = b.c0 + (czz * n1 + cyy) * n0;
+        int fx = wrap_cell(cx + b.ofs[0][0], n0);
+        int last = fx + nofs0 - 1;
+        int lastA = last < n0 ? last : n0 - 1;
         int a0 = v.start[rowbase + fx];
         int la = v.start[rowbase + lastA + 1] - a0;
         int b0 = v.start[rowbase];
-        int lb = last >= v.n[0] ? v.start[rowbase + (last - v.n[0]) + 1] - b0 : 0;
+        int lb = last >= n0 ? v.start[rowbase + (last - n0) + 1] - b0 : 0;
         sA[sg] = a0;
         lA[sg] = la;
         sB[sg] = b0;
@@ -282,14 +315,16 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
         for (int sg = 1; sg <= S; ++sg) pre[sg] += pre[sg - 1];
     }
     __syncwarp();
-    int4 *gt = v.seg_tab + (size_t)c * S;
-    for (int sg = lane; sg < S; sg += 32) gt[sg] = make_int4(sA[sg], lA[sg], sB[sg], pre[sg + 1]);
-    const int s0 = v.start[c], s1 = v.start[c + 1];
     const int M = pre[S];
+    int4 *gt = v.seg_tab + (size_t)c * v.S;
+    for (int sg = lane; sg < v.S; sg += 32)
+        gt[sg] = sg < S ? make_int4(sA[sg], lA[sg], sB[sg], pre[sg + 1]) : make_int4(0, 0, 0, M);
+    const int s0 = v.start[c], s1 = v.start[c + 1];
     if (s1 == s0) return;
     // the masks index this cell's candidate sequence: remember the cell until the
     // next build, however far the particle drifts meanwhile
-    for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = pack_cell(cx, cy, cz);
+    for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
+    RepScalars &rsc = v.rs[r];
     if (M > v.Mcap) {
         // too many candidates for the masks: flag it and leave these particles with
         // empty rows so that no kernel decodes a mask that was not written
@@ -299,10 +334,11 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
         }
         if (lane == 0) {
             atomicOr(&v.sc->flags, kFlagCellOverflow);
-            atomicMax(&v.sc->m_max, M);
+            atomicMax(&rsc.m_max, M);
         }
         return;
     }
+    const float h[3] = {b.h[0], b.h[1], b.h[2]};
     const int nchunk = (M + 31) >> 5;
     const bool full = v.full_list != 0;
     const size_t N = (size_t)v.N;
@@ -329,7 +365,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
             // particle q's shell and core words
             unsigned my_shell = 0u, my_core = 0u;
             for (int q = 0; q < mm; ++q) {
-                PairGeom g = pair_geom(s_pos[warp][q], pj, v.h);
+                PairGeom g = pair_geom(s_pos[warp][q], pj, h);
                 const bool other = valid && j != base + q;
                 bool in_core, in_shell;
                 if (full) {
@@ -376,12 +412,12 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
         wss += __shfl_xor_sync(0xffffffffu, wss, o);
     }
     if (lane == 0) {
-        atomicMax(&v.sc->nc_max, wmc);
-        atomicMax(&v.sc->ns_max, wms);
-        atomicMax(&v.sc->m_max, M);
-        atomicAdd(&v.sc->nc_sum, wsc);
-        atomicAdd(&v.sc->ns_sum, wss);
-        atomicAdd(&v.sc->m_sum, (unsigned long long)M * (unsigned long long)(s1 - s0));
+        atomicMax(&rsc.nc_max, wmc);
+        atomicMax(&rsc.ns_max, wms);
+        atomicMax(&rsc.m_max, M);
+        atomicAdd(&rsc.nc_sum, wsc);
+        atomicAdd(&rsc.ns_sum, wss);
+        atomicAdd(&rsc.m_sum, (unsigned long long)M * (unsigned long long)(s1 - s0));
     }
 }
 
@@ -395,9 +431,16 @@ __global__ void k_set_condition(View v, cudaGraphConditionalHandle h)
 __global__ void k_finish(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    v.sc->rebuild = 0;
-    v.sc->n_rebuild += 1;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < v.R && active(v, conditional, r)) {
+        v.rs[r].rebuild = 0;
+        v.rs[r].n_rebuild += 1;
+    }
 }
+
+// Runs after k_finish: the context-wide flag is cleared only once every replica
+// has read it.
+__global__ void k_finish_all(View v) { v.sc->rebuild = 0; }
 
 } // namespace
 
@@ -417,7 +460,8 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_permute<<<gN, kBlock, 0, s>>>(v, cond);
     k_copy_back<<<gN, kBlock, 0, s>>>(v, cond);
     k_build_lists<<<ceil_div(v.ncell, kBuildWarps), kBuildWarps * 32, 0, s>>>(v, cond);
-    k_finish<<<1, 1, 0, s>>>(v, cond);
+    k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
+    k_finish_all<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();
 }
 

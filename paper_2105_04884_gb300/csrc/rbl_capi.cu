@@ -1,16 +1,19 @@
 // rbl_capi.cu -- host side of the C ABI declared in include/rbl.h.
 //
 // The context lives in host memory; every device array is carved out of the
-// caller's workspace.  A step of Algorithm 1 is enqueued as: fused kick/drift/
-// thermostat kernel, the (device-conditional) rebuild chain, the force kernel and
-// its reduction.  The steady-state step is captured once in a CUDA graph and
-// replayed; the step counter lives in device memory so replays stay valid.
+// caller's workspace.  A context holds R >= 1 independent replicas (rbl_create
+// makes R = 1); each kernel launch covers all of them.  A step of Algorithm 1 is
+// enqueued as: fused kick/drift/thermostat kernel, the (device-conditional)
+// rebuild chain, the force kernel and its reduction.  The steady-state step is
+// captured once in a CUDA graph and replayed; the step counter lives in device
+// memory so replays stay valid.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "rbl_internal.cuh"
@@ -20,18 +23,29 @@ using namespace rbl;
 namespace {
 
 const double kPi = 3.14159265358979323846264338327950288;
+constexpr long long kMaxSlots = 1ll << 30;  // particle slots of a context (int indices, int32 rows)
 
-struct Layout {
-    size_t off[32];
+// Sizes and offsets of every array of a context's workspace.
+struct Plan {
+    size_t off[40];
     int n;
     size_t total;
-    int cap_c, W, S, Mcap, ncell, n3[3], nofs3[3], ntiles, nblk;
+    int R, N, ntile, ncell, cap_c, W, S, Mcap, n_scan_blocks;
+    long long n_real;
     size_t staging_bytes;
+};
+
+// Cell grid and candidate statistics of one replica.
+struct Geo {
+    int n3[3], nofs3[3], S, ncell, mcap;
+    double core_mean;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+long long round_up_ll(long long x, long long m) { return (x + m - 1) / m * m; }
 
 void set_err(rbl_ctx *c, const char *fmt, ...)
 {
@@ -42,13 +56,14 @@ void set_err(rbl_ctx *c, const char *fmt, ...)
     va_end(ap);
 }
 
+#define BAD(...)                                       \
+    do {                                               \
+        if (err) snprintf(err, errlen, __VA_ARGS__);   \
+        return RBL_EINVAL;                             \
+    } while (0)
+
 rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
 {
-#define BAD(...)                                   \
-    do {                                           \
-        if (err) snprintf(err, errlen, __VA_ARGS__); \
-        return RBL_EINVAL;                         \
-    } while (0)
     if (!p) BAD("params is NULL");
     if (N < 2) BAD("N must be >= 2 (got %d)", N);
     const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma};
@@ -65,70 +80,205 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
         if (!(p->L[a] >= 2.0 * (p->r_s + p->skin)))
             BAD("box length L[%d]=%g is below 2 (r_s + skin) = %g", a, p->L[a], 2.0 * (p->r_s + p->skin));
     if (p->cap_core < 0 || p->cap_stencil < 0) BAD("capacities must be >= 0");
-    for (int a = 0; a < 3; ++a)
-        if (std::floor(p->L[a] * p->cells_per_cutoff / (p->r_s + p->skin)) > (double)(1 << kCellBits))
-            BAD("box too large: more than %d cells along axis %d", 1 << kCellBits, a);
+    double cells = 1.0;
+    for (int a = 0; a < 3; ++a) cells *= std::floor(p->L[a] * p->cells_per_cutoff / (p->r_s + p->skin));
+    if (cells > (double)(1 << 28)) BAD("box too large: %.0f cells", cells);
     return RBL_OK;
-#undef BAD
 }
 
-Layout make_layout(const rbl_params *p, int N)
+// Replicas share everything but the box, the temperature, the seed and N.
+rbl_status validate_batch(const rbl_params *prm, int R, const int *N, char *err, size_t errlen)
 {
-    Layout L{};
-    double V = p->L[0] * p->L[1] * p->L[2];
-    double rho = N / V;
-    double rcut = p->r_s + p->skin;
-    double core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
-    L.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
-    int K = p->cells_per_cutoff;
+    if (!prm || !N || R < 1) BAD("need R >= 1 replicas with params and sizes (got R=%d)", R);
+    long long slots = 0;
+    for (int r = 0; r < R; ++r) {
+        rbl_status st = validate(&prm[r], N[r], err, errlen);
+        if (st != RBL_OK) return st;
+        const rbl_params &a = prm[0], &b = prm[r];
+        if (a.r_c != b.r_c || a.r_s != b.r_s || a.skin != b.skin || a.p != b.p || a.dt != b.dt ||
+            a.gamma != b.gamma || a.precision != b.precision || a.full_list != b.full_list ||
+            a.subtract_net_force != b.subtract_net_force || a.cells_per_cutoff != b.cells_per_cutoff ||
+            a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil)
+            BAD("replica %d differs from replica 0 in a shared parameter (only L, T, seed may differ)", r);
+        slots += round_up_ll(N[r], kTile);
+    }
+    if (slots > kMaxSlots) BAD("too many particles: %lld slots (limit %lld)", slots, kMaxSlots);
+    return RBL_OK;
+}
+#undef BAD
+
+Geo replica_geo(const rbl_params *p, int N)
+{
+    Geo g{};
+    const double rho = N / (p->L[0] * p->L[1] * p->L[2]);
+    const double rcut = p->r_s + p->skin;
+    const int K = p->cells_per_cutoff;
     long long nc = 1;
     double span = 1.0;
     for (int a = 0; a < 3; ++a) {
         int n = (int)std::floor(p->L[a] * (double)K / rcut);
         if (n < 1) n = 1;
-        L.n3[a] = n;
-        L.nofs3[a] = n >= 2 * K + 1 ? 2 * K + 1 : n;
-        span *= L.nofs3[a] * (p->L[a] / n);
+        g.n3[a] = n;
+        g.nofs3[a] = n >= 2 * K + 1 ? 2 * K + 1 : n;
+        span *= g.nofs3[a] * (p->L[a] / n);
         nc *= n;
     }
-    L.ncell = (int)nc;
-    L.S = L.nofs3[1] * L.nofs3[2];
+    g.ncell = (int)nc;
+    g.S = g.nofs3[1] * g.nofs3[2];
     int mcap = p->cap_stencil > 0 ? p->cap_stencil : (int)std::ceil(1.3 * rho * span + 96.0);
-    if (mcap > N) mcap = N;
-    L.Mcap = round_up(mcap, 32);
-    L.W = L.Mcap / 32;
-    L.ntiles = (L.ncell + 2047) / 2048;
-    L.nblk = (N + kBlock - 1) / kBlock;
-    size_t Nz = (size_t)N;
-    L.staging_bytes = 48 * Nz;
-    size_t batch_bytes = 4 * Nz * (size_t)(p->p + 1);
-    if (batch_bytes > L.staging_bytes) L.staging_bytes = batch_bytes;
-    if (L.staging_bytes < (size_t)L.nblk * 32) L.staging_bytes = (size_t)L.nblk * 32;
-    if (L.staging_bytes < (1u << 20)) L.staging_bytes = 1u << 20;
+    g.mcap = mcap > N ? N : mcap;
+    g.core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
+    return g;
+}
+
+Plan make_plan(const rbl_params *prm, int R, const int *Ns)
+{
+    Plan P{};
+    P.R = R;
+    long long slots = 0, cells = 0, n_real = 0;
+    int S = 1, mcap = 32;
+    double core_mean = 0.0;
+    for (int r = 0; r < R; ++r) {
+        Geo g = replica_geo(&prm[r], Ns[r]);
+        slots += round_up_ll(Ns[r], kTile);
+        cells += g.ncell + 1;
+        n_real += Ns[r];
+        S = g.S > S ? g.S : S;
+        mcap = g.mcap > mcap ? g.mcap : mcap;
+        core_mean = g.core_mean > core_mean ? g.core_mean : core_mean;
+    }
+    const rbl_params *p = &prm[0];
+    P.N = (int)slots;
+    P.ntile = P.N / kTile;
+    P.ncell = (int)cells;
+    P.n_real = n_real;
+    P.S = S;
+    P.Mcap = round_up(mcap, 32);
+    P.W = P.Mcap / 32;
+    P.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
+    P.n_scan_blocks = (P.ncell + 2047) / 2048;
+    const size_t Nz = (size_t)P.N;
+    size_t st = 48 * (size_t)n_real;                   // packed x and v (host copies)
+    if (st < 4 * Nz * (size_t)(p->p + 1)) st = 4 * Nz * (size_t)(p->p + 1); // batch hook
+    if (st < (size_t)P.ntile * 32) st = (size_t)P.ntile * 32;               // kinetic partials
+    if (st < (1u << 20)) st = 1u << 20;
+    P.staging_bytes = st;
     const size_t sizes[] = {
         24 * Nz, 24 * Nz, 24 * Nz, 24 * Nz,         // x, x_alt, v, v_alt
         4 * Nz, 4 * Nz,                             // tag, tag_alt
         16 * Nz, 16 * Nz, 16 * Nz,                  // pos, pos_alt, ubuild
         24 * Nz,                                    // F
         4 * Nz, 4 * Nz,                             // cell, order
-        4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), 4 * ((size_t)L.ncell + 1), // counts, start, fill
-        4 * ((size_t)L.ntiles + 1),                 // blocksums
-        16 * (size_t)L.ncell * (size_t)L.S,         // seg_tab
-        4 * Nz * (size_t)L.cap_c, 4 * Nz,           // core, n_core
-        4 * Nz * (size_t)L.W, 4 * Nz,               // mask, n_shell
+        4 * ((size_t)P.ncell + 1), 4 * ((size_t)P.ncell + 1), 4 * ((size_t)P.ncell + 1), // counts, start, fill
+        4 * ((size_t)P.n_scan_blocks + 1),          // blocksums
+        16 * (size_t)P.ncell * (size_t)P.S,         // seg_tab
+        4 * Nz * (size_t)P.cap_c, 4 * Nz,           // core, n_core
+        4 * Nz * (size_t)P.W, 4 * Nz,               // mask, n_shell
         4 * Nz,                                     // hcell
-        64 * (size_t)((N + kMinBlock - 1) / kMinBlock), // partials [blocks][8] doubles, any block size >= kMinBlock
-        sizeof(DevScalars),                         // scalars
-        L.staging_bytes,                            // staging
+        64 * (Nz / kMinBlock),                      // partials [blocks][8] doubles, any block size >= kMinBlock
+        sizeof(Box) * (size_t)R,                    // box
+        8 * (size_t)P.ntile,                        // tile
+        4 * (size_t)P.ncell,                        // cell_rep
+        sizeof(RepScalars) * (size_t)R,             // rs
+        sizeof(DevScalars),                         // sc
+        P.staging_bytes,                            // staging
     };
-    L.n = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    P.n = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t o = 0;
-    for (int k = 0; k < L.n; ++k) {
-        L.off[k] = o;
+    for (int k = 0; k < P.n; ++k) {
+        P.off[k] = o;
         o += align256(sizes[k]);
     }
-    L.total = o;
-    return L;
+    P.total = o;
+    return P;
+}
+
+// Replica r's table entry: box, thermostat amplitude, seed, cell grid and stencil.
+Box make_box(const rbl_params *p, int N, int first, int c0, int in0)
+{
+    Box b{};
+    Geo g = replica_geo(p, N);
+    const int K = p->cells_per_cutoff;
+    for (int a = 0; a < 3; ++a) {
+        b.L[a] = p->L[a];
+        b.inv[a] = 4294967296.0 / p->L[a];
+        b.h[a] = (float)(p->L[a] / 4294967296.0);
+        b.n[a] = g.n3[a];
+        b.nofs[a] = g.nofs3[a];
+        for (int o = 0; o < g.nofs3[a]; ++o) b.ofs[a][o] = g.n3[a] >= 2 * K + 1 ? o - K : o;
+    }
+    const double c1 = std::exp(-p->gamma * p->dt);
+    b.c2f = (float)std::sqrt((1.0 - c1 * c1) * p->T);
+    b.T = p->T;
+    b.seed = p->seed;
+    b.N = N;
+    b.first = first;
+    b.slots = round_up(N, kTile);
+    b.in0 = in0;
+    b.c0 = c0;
+    b.ncell = g.ncell;
+    b.S = g.S;
+    return b;
+}
+
+// Kernel view over a laid-out workspace (the shared parameters come from prm).
+void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
+{
+    v = View{};
+    v.N = P.N;
+    v.R = P.R;
+    v.ntile = P.ntile;
+    v.p = prm->p;
+    v.K = prm->cells_per_cutoff;
+    v.cap_c = P.cap_c;
+    v.W = P.W;
+    v.S = P.S;
+    v.Mcap = P.Mcap;
+    v.full_list = prm->full_list ? 1 : 0;
+    v.precision = prm->precision;
+    v.subtract = prm->subtract_net_force ? 1 : 0;
+    v.ncell = P.ncell;
+    const double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
+    const double lo = rc - sk > 0.0 ? rc - sk : 0.0;
+    v.t_core_list = (float)((rc + sk) * (rc + sk));
+    v.t_shell_lo = (float)(lo * lo);
+    v.t_cut_list = (float)((rs + sk) * (rs + sk));
+    v.t_rc2 = (float)(rc * rc);
+    v.t_rs2 = (float)(rs * rs);
+    v.t_disp = (float)(0.25 * sk * sk);
+    v.dt = prm->dt;
+    v.gamma = prm->gamma;
+    v.c1 = std::exp(-prm->gamma * prm->dt);
+    int k = 0;
+    v.x = (double *)(base + P.off[k++]);
+    v.x_alt = (double *)(base + P.off[k++]);
+    v.v = (double *)(base + P.off[k++]);
+    v.v_alt = (double *)(base + P.off[k++]);
+    v.tag = (int *)(base + P.off[k++]);
+    v.tag_alt = (int *)(base + P.off[k++]);
+    v.pos = (int4 *)(base + P.off[k++]);
+    v.pos_alt = (int4 *)(base + P.off[k++]);
+    v.ubuild = (int4 *)(base + P.off[k++]);
+    v.F = (void *)(base + P.off[k++]);
+    v.cell = (int *)(base + P.off[k++]);
+    v.order = (int *)(base + P.off[k++]);
+    v.counts = (int *)(base + P.off[k++]);
+    v.start = (int *)(base + P.off[k++]);
+    v.fill = (int *)(base + P.off[k++]);
+    v.blocksums = (int *)(base + P.off[k++]);
+    v.seg_tab = (int4 *)(base + P.off[k++]);
+    v.core = (int *)(base + P.off[k++]);
+    v.n_core = (int *)(base + P.off[k++]);
+    v.mask = (unsigned *)(base + P.off[k++]);
+    v.n_shell = (int *)(base + P.off[k++]);
+    v.hcell = (int *)(base + P.off[k++]);
+    v.partials = (double *)(base + P.off[k++]);
+    v.box = (const Box *)(base + P.off[k++]);
+    v.tile = (const int2 *)(base + P.off[k++]);
+    v.cell_rep = (const int *)(base + P.off[k++]);
+    v.rs = (RepScalars *)(base + P.off[k++]);
+    v.sc = (DevScalars *)(base + P.off[k++]);
+    v.staging = (double *)(base + P.off[k++]);
 }
 
 #define CK(call)                                                                         \
@@ -140,21 +290,30 @@ Layout make_layout(const rbl_params *p, int N)
         }                                                                                \
     } while (0)
 
-rbl_status read_scalars(rbl_ctx *ctx)
+rbl_status read_scalars(rbl_ctx *ctx, bool replicas = false)
 {
     CK(cudaMemcpyAsync(ctx->h_sc, ctx->view.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    if (replicas)
+        CK(cudaMemcpyAsync(ctx->h_rs, ctx->view.rs, sizeof(RepScalars) * (size_t)ctx->R, cudaMemcpyDeviceToHost,
+                           ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RBL_OK;
 }
 
-rbl_status check_flags(rbl_ctx *ctx)
+rbl_status check_flags(rbl_ctx *ctx, bool replicas = false)
 {
-    rbl_status st = read_scalars(ctx);
+    rbl_status st = read_scalars(ctx, replicas);
     if (st != RBL_OK) return st;
     unsigned f = ctx->h_sc->flags;
     if (f & (kFlagOverflow | kFlagCellOverflow)) {
-        set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest stencil population %d / cap %d)",
-                ctx->h_sc->nc_max, ctx->view.cap_c, ctx->h_sc->m_max, ctx->view.Mcap);
+        if (!replicas) read_scalars(ctx, true);
+        int nc = 0, m = 0;
+        for (int r = 0; r < ctx->R; ++r) {
+            nc = ctx->h_rs[r].nc_max > nc ? ctx->h_rs[r].nc_max : nc;
+            m = ctx->h_rs[r].m_max > m ? ctx->h_rs[r].m_max : m;
+        }
+        set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest stencil population %d / cap %d)", nc,
+                ctx->view.cap_c, m, ctx->view.Mcap);
         return RBL_EOVERFLOW;
     }
     if (f & kFlagNonFinite) {
@@ -259,7 +418,9 @@ rbl_status ensure_graph(rbl_ctx *ctx)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, mode);
         if (e == cudaSuccess) {
-            cudaError_t ec = launch_rebuild(ctx->view, ctx->n_scan_blocks, false, s);
+            // conditional kernels: inside the IF body some replica is due, and each
+            // kernel still skips the replicas whose own flag is down
+            cudaError_t ec = launch_rebuild(ctx->view, ctx->n_scan_blocks, true, s);
             cudaGraph_t bout = nullptr;
             e = cudaStreamEndCapture(s, &bout);
             if (ec != cudaSuccess) e = ec;
@@ -274,6 +435,77 @@ rbl_status ensure_graph(rbl_ctx *ctx)
         return RBL_ECUDA;
     }
     ctx->graph_exec = ex;
+    return RBL_OK;
+}
+
+
+rbl_status create_impl(const rbl_params *prm, int R, const int *Ns, void *workspace, size_t workspace_bytes,
+                       void *stream, rbl_ctx **out)
+{
+    if (!out) return RBL_EINVAL;
+    *out = nullptr;
+    rbl_ctx *ctx = new (std::nothrow) rbl_ctx();
+    if (!ctx) return RBL_ENOMEM;
+    rbl_status st = validate_batch(prm, R, Ns, ctx->err, sizeof(ctx->err));
+    if (st != RBL_OK) {
+        // keep the handle so the caller can read the message; it holds no device state
+        *out = ctx;
+        return st;
+    }
+    const Plan P = make_plan(prm, R, Ns);
+    if (!workspace || workspace_bytes < P.total || ((uintptr_t)workspace & 255u)) {
+        set_err(ctx, "workspace must be 256-byte aligned and at least %zu bytes (got %zu)", P.total,
+                workspace_bytes);
+        *out = ctx;
+        return workspace_bytes < P.total ? RBL_ENOMEM : RBL_EINVAL;
+    }
+    ctx->prm = prm[0];
+    ctx->stream = (cudaStream_t)stream;
+    ctx->R = R;
+    ctx->n_real = P.n_real;
+    ctx->n_scan_blocks = P.n_scan_blocks;
+    ctx->step = 0;
+    ctx->staging_bytes = P.staging_bytes;
+    ctx->h_sc = new (std::nothrow) DevScalars();
+    ctx->h_rs = new (std::nothrow) RepScalars[R]();
+    ctx->h_box = new (std::nothrow) Box[R]();
+    ctx->h_tile = new (std::nothrow) int2[P.ntile]();
+    ctx->h_cell_rep = new (std::nothrow) int[P.ncell]();
+    if (!ctx->h_sc || !ctx->h_rs || !ctx->h_box || !ctx->h_tile || !ctx->h_cell_rep) {
+        set_err(ctx, "host tables: out of memory");
+        *out = ctx;
+        return RBL_ENOMEM;
+    }
+    // replica table: replicas in order, each on whole tiles and followed by its pad cell
+    int first = 0, c0 = 0, in0 = 0;
+    for (int r = 0; r < R; ++r) {
+        Box &b = ctx->h_box[r];
+        b = make_box(&prm[r], Ns[r], first, c0, in0);
+        for (int t = first / kTile; t < (first + b.slots) / kTile; ++t) ctx->h_tile[t] = make_int2(r, first + b.N);
+        for (int c = c0; c <= c0 + b.ncell; ++c) ctx->h_cell_rep[c] = r;
+        first += b.slots;
+        c0 += b.ncell + 1;
+        in0 += b.N;
+    }
+    View &v = ctx->view;
+    assign_view(v, &prm[0], P, (char *)workspace);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync((void *)v.box, ctx->h_box, sizeof(Box) * (size_t)R, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)v.tile, ctx->h_tile, 8 * (size_t)P.ntile, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)v.cell_rep, ctx->h_cell_rep, 4 * (size_t)P.ncell, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.sc, 0, sizeof(DevScalars), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.rs, 0, sizeof(RepScalars) * (size_t)R, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)P.N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * ((size_t)P.N / kMinBlock), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_err(ctx, "initialisation failed: %s", cudaGetErrorString(e));
+        *out = ctx;
+        return RBL_ECUDA;
+    }
+    *out = ctx;
     return RBL_OK;
 }
 
@@ -296,125 +528,39 @@ void rbl_params_default(rbl_params *prm)
 
 rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes)
 {
+    return rbl_workspace_size_batch(prm, 1, &N, bytes);
+}
+
+rbl_status rbl_workspace_size_batch(const rbl_params *prm, int R, const int *N, size_t *bytes)
+{
     if (!bytes) return RBL_EINVAL;
-    rbl_status st = validate(prm, N, nullptr, 0);
+    rbl_status st = validate_batch(prm, R, N, nullptr, 0);
     if (st != RBL_OK) return st;
-    *bytes = make_layout(prm, N).total;
+    *bytes = make_plan(prm, R, N).total;
     return RBL_OK;
 }
 
 rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,
                       rbl_ctx **out)
 {
-    if (!out) return RBL_EINVAL;
-    *out = nullptr;
-    rbl_ctx *ctx = new (std::nothrow) rbl_ctx();
-    if (!ctx) return RBL_ENOMEM;
-    rbl_status st = validate(prm, N, ctx->err, sizeof(ctx->err));
-    if (st != RBL_OK) {
-        // keep the handle so the caller can read the message; it holds no device state
-        *out = ctx;
-        return st;
-    }
-    Layout L = make_layout(prm, N);
-    if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) {
-        set_err(ctx, "workspace must be 256-byte aligned and at least %zu bytes (got %zu)", L.total,
-                workspace_bytes);
-        *out = ctx;
-        return workspace_bytes < L.total ? RBL_ENOMEM : RBL_EINVAL;
-    }
-    ctx->prm = *prm;
-    ctx->stream = (cudaStream_t)stream;
-    ctx->nblk = L.nblk;
-    ctx->n_scan_blocks = L.ntiles;
-    ctx->step = 0;
-    ctx->h_sc = new DevScalars();
-    char *base = (char *)workspace;
-    View &v = ctx->view;
-    v.N = N;
-    v.p = prm->p;
-    v.K = prm->cells_per_cutoff;
-    v.cap_c = L.cap_c;
-    v.W = L.W;
-    v.S = L.S;
-    v.Mcap = L.Mcap;
-    v.full_list = prm->full_list ? 1 : 0;
-    v.precision = prm->precision;
-    v.subtract = prm->subtract_net_force ? 1 : 0;
-    v.ncell = L.ncell;
-    for (int a = 0; a < 3; ++a) {
-        int n = L.n3[a], K = prm->cells_per_cutoff;
-        v.n[a] = n;
-        v.nofs[a] = L.nofs3[a];
-        for (int o = 0; o < L.nofs3[a]; ++o) v.ofs[a][o] = n >= 2 * K + 1 ? o - K : o;
-        v.L[a] = prm->L[a];
-        v.inv[a] = 4294967296.0 / prm->L[a];
-        v.h[a] = (float)(prm->L[a] / 4294967296.0);
-    }
-    for (int sg = 0; sg < L.S; ++sg) {
-        v.seg_oz[sg] = (signed char)(sg / L.nofs3[1]);
-        v.seg_oy[sg] = (signed char)(sg % L.nofs3[1]);
-    }
-    double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
-    double lo = rc - sk > 0.0 ? rc - sk : 0.0;
-    v.t_core_list = (float)((rc + sk) * (rc + sk));
-    v.t_shell_lo = (float)(lo * lo);
-    v.t_cut_list = (float)((rs + sk) * (rs + sk));
-    v.t_rc2 = (float)(rc * rc);
-    v.t_rs2 = (float)(rs * rs);
-    v.t_disp = (float)(0.25 * sk * sk);
-    v.dt = prm->dt;
-    v.T = prm->T;
-    v.gamma = prm->gamma;
-    v.c1 = std::exp(-prm->gamma * prm->dt);
-    v.c2f = (float)std::sqrt((1.0 - v.c1 * v.c1) * prm->T);
-    v.seed = prm->seed;
-    int k = 0;
-    v.x = (double *)(base + L.off[k++]);
-    v.x_alt = (double *)(base + L.off[k++]);
-    v.v = (double *)(base + L.off[k++]);
-    v.v_alt = (double *)(base + L.off[k++]);
-    v.tag = (int *)(base + L.off[k++]);
-    v.tag_alt = (int *)(base + L.off[k++]);
-    v.pos = (int4 *)(base + L.off[k++]);
-    v.pos_alt = (int4 *)(base + L.off[k++]);
-    v.ubuild = (int4 *)(base + L.off[k++]);
-    v.F = (void *)(base + L.off[k++]);
-    v.cell = (int *)(base + L.off[k++]);
-    v.order = (int *)(base + L.off[k++]);
-    v.counts = (int *)(base + L.off[k++]);
-    v.start = (int *)(base + L.off[k++]);
-    v.fill = (int *)(base + L.off[k++]);
-    v.blocksums = (int *)(base + L.off[k++]);
-    v.seg_tab = (int4 *)(base + L.off[k++]);
-    v.core = (int *)(base + L.off[k++]);
-    v.n_core = (int *)(base + L.off[k++]);
-    v.mask = (unsigned *)(base + L.off[k++]);
-    v.n_shell = (int *)(base + L.off[k++]);
-    v.hcell = (int *)(base + L.off[k++]);
-    v.partials = (double *)(base + L.off[k++]);
-    v.sc = (DevScalars *)(base + L.off[k++]);
-    v.staging = (double *)(base + L.off[k++]);
-    ctx->staging_bytes = L.staging_bytes;
-    cudaError_t e = cudaMemsetAsync(v.sc, 0, sizeof(DevScalars), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)N, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * (size_t)((N + kMinBlock - 1) / kMinBlock), ctx->stream);
-    if (e != cudaSuccess) {
-        set_err(ctx, "initialisation failed: %s", cudaGetErrorString(e));
-        *out = ctx;
-        return RBL_ECUDA;
-    }
-    *out = ctx;
-    return RBL_OK;
+    return create_impl(prm, 1, &N, workspace, workspace_bytes, stream, out);
 }
+
+rbl_status rbl_create_batch(const rbl_params *prm, int R, const int *N, void *workspace, size_t workspace_bytes,
+                            void *stream, rbl_ctx **out)
+{
+    return create_impl(prm, R, N, workspace, workspace_bytes, stream, out);
+}
+
+int rbl_replicas(const rbl_ctx *ctx) { return ctx ? ctx->R : 0; }
 
 rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long long step, int ptr_is_device)
 {
     if (!ctx || !x || step < 0) return RBL_EINVAL;
-    size_t bytes = 24 * (size_t)ctx->view.N;
+    size_t bytes = 24 * (size_t)ctx->n_real;
     const double *dx = x, *dv = v;
     if (!ptr_is_device) {
-        double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->view.N;
+        double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->n_real;
         CK(cudaMemcpyAsync(sx, x, bytes, cudaMemcpyHostToDevice, ctx->stream));
         if (v) CK(cudaMemcpyAsync(sv, v, bytes, cudaMemcpyHostToDevice, ctx->stream));
         dx = sx;
@@ -423,8 +569,8 @@ rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long lo
     DevScalars z{};
     *ctx->h_sc = z;
     ctx->h_sc->step = (unsigned long long)step;
-    ctx->h_sc->n_rebuild = 0;
     CK(cudaMemcpyAsync(ctx->view.sc, ctx->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->view.rs, 0, sizeof(RepScalars) * (size_t)ctx->R, ctx->stream));
     CK(launch_load_state(ctx->view, dx, dv, ctx->stream));
     ctx->step = step;
     ctx->lists_valid = 0;
@@ -442,12 +588,12 @@ rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, in
     if (!ctx) return RBL_EINVAL;
     if (step) *step = ctx->step;
     if (!x && !v) return RBL_OK;
-    size_t bytes = 24 * (size_t)ctx->view.N;
+    size_t bytes = 24 * (size_t)ctx->n_real;
     if (ptr_is_device) {
         CK(launch_store_state(ctx->view, x, v, ctx->stream));
         return RBL_OK;
     }
-    double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->view.N;
+    double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->n_real;
     CK(launch_store_state(ctx->view, x ? sx : nullptr, v ? sv : nullptr, ctx->stream));
     if (x) CK(cudaMemcpyAsync(x, sx, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     if (v) CK(cudaMemcpyAsync(v, sv, bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -475,7 +621,7 @@ rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device)
             CK(launch_store_forces(ctx->view, F_out, ctx->stream));
         } else {
             CK(launch_store_forces(ctx->view, ctx->view.staging, ctx->stream));
-            CK(cudaMemcpyAsync(F_out, ctx->view.staging, 24 * (size_t)ctx->view.N, cudaMemcpyDeviceToHost,
+            CK(cudaMemcpyAsync(F_out, ctx->view.staging, 24 * (size_t)ctx->n_real, cudaMemcpyDeviceToHost,
                                ctx->stream));
             return check_flags(ctx);
         }
@@ -530,35 +676,39 @@ rbl_status rbl_step(rbl_ctx *ctx, int n)
     return check_flags(ctx);
 }
 
+
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out)
 {
     if (!ctx || !out) return RBL_EINVAL;
     rbl_status st = ensure_force(ctx, true);
     if (st != RBL_OK) return st;
     CK(launch_kinetic(ctx->view, ctx->stream));
-    st = check_flags(ctx);
+    st = check_flags(ctx, true);
     if (st != RBL_OK) return st;
-    const DevScalars &s = *ctx->h_sc;
-    const View &v = ctx->view;
-    double V = v.L[0] * v.L[1] * v.L[2];
-    double rho = v.N / V;
-    std::memset(out, 0, sizeof(*out));
-    out->U_est = s.energy;
-    out->W_est = s.virial;
-    out->K = 0.5 * s.ksum;
-    out->T_kin = s.ksum / (3.0 * v.N);
-    out->P = rho * out->T_kin + s.virial / (3.0 * V);
-    double rs = ctx->prm.r_s, i3 = 1.0 / (rs * rs * rs), i9 = i3 * i3 * i3;
-    out->U_tail = 8.0 / 3.0 * kPi * rho * (i9 / 3.0 - i3);
-    out->P_tail = 16.0 / 3.0 * kPi * rho * rho * (2.0 * i9 / 3.0 - i3);
-    for (int a = 0; a < 3; ++a) out->net_momentum[a] = s.psum[a];
-    out->step = (long long)s.step;
-    out->n_rebuild = s.n_rebuild;
-    out->Ns_mean = (double)s.ns_sum / v.N;
-    out->Nc_mean = (double)s.nc_sum / v.N;
-    out->Mc_mean = (double)s.m_sum / v.N;
-    out->Ns_max = s.ns_max;
-    out->Nc_max = s.nc_max;
+    const double rs = ctx->prm.r_s, i3 = 1.0 / (rs * rs * rs), i9 = i3 * i3 * i3;
+    for (int r = 0; r < ctx->R; ++r) {
+        const RepScalars &s = ctx->h_rs[r];
+        const Box &b = ctx->h_box[r];
+        const double V = b.L[0] * b.L[1] * b.L[2];
+        const double rho = b.N / V;
+        rbl_obs &o = out[r];
+        std::memset(&o, 0, sizeof(o));
+        o.U_est = s.energy;
+        o.W_est = s.virial;
+        o.K = 0.5 * s.ksum;
+        o.T_kin = s.ksum / (3.0 * b.N);
+        o.P = rho * o.T_kin + s.virial / (3.0 * V);
+        o.U_tail = 8.0 / 3.0 * kPi * rho * (i9 / 3.0 - i3);
+        o.P_tail = 16.0 / 3.0 * kPi * rho * rho * (2.0 * i9 / 3.0 - i3);
+        for (int a = 0; a < 3; ++a) o.net_momentum[a] = s.psum[a];
+        o.step = (long long)ctx->h_sc->step;
+        o.n_rebuild = s.n_rebuild;
+        o.Ns_mean = (double)s.ns_sum / b.N;
+        o.Nc_mean = (double)s.nc_sum / b.N;
+        o.Mc_mean = (double)s.m_sum / b.N;
+        o.Ns_max = s.ns_max;
+        o.Nc_max = s.nc_max;
+    }
     return RBL_OK;
 }
 
@@ -568,10 +718,12 @@ rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W)
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
     CK(launch_exact_energy(ctx->view, ctx->stream));
-    st = check_flags(ctx);
+    st = check_flags(ctx, true);
     if (st != RBL_OK) return st;
-    *U = ctx->h_sc->u_exact;
-    *W = ctx->h_sc->w_exact;
+    for (int r = 0; r < ctx->R; ++r) {
+        U[r] = ctx->h_rs[r].u_exact;
+        W[r] = ctx->h_rs[r].w_exact;
+    }
     return RBL_OK;
 }
 
@@ -584,22 +736,28 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
     st = check_flags(ctx);
     if (st != RBL_OK) return st;
     const View &v = ctx->view;
-    size_t N = (size_t)v.N;
+    const size_t N = (size_t)v.N;
     std::vector<int> tag(N), cnt(N);
     CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(cnt.data(), kind == 0 ? v.n_core : v.n_shell, 4 * N, cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < N; ++i)
-        if (cnt[i] > cap) {
-            set_err(ctx, "row of tag %d has %d entries, more than cap %d", tag[i], cnt[i], cap);
+    // packed row of slot i, or -1 for a padding slot
+    std::vector<long long> row_of(N);
+    for (size_t i = 0; i < N; ++i) {
+        const int2 t = ctx->h_tile[i >> kTileShift];
+        row_of[i] = (long long)i < t.y ? (long long)ctx->h_box[t.x].in0 + tag[i] : -1;
+        if (row_of[i] >= 0 && cnt[i] > cap) {
+            set_err(ctx, "row %lld has %d entries, more than cap %d", row_of[i], cnt[i], cap);
             return RBL_EOVERFLOW;
         }
+    }
     if (kind == 0) {
         std::vector<int> core(N * (size_t)v.cap_c);
         CK(cudaMemcpy(core.data(), v.core, core.size() * 4, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < N; ++i) {
-            int t = tag[i];
+            if (row_of[i] < 0) continue;
+            const size_t t = (size_t)row_of[i];
             counts[t] = cnt[i];
-            for (int k = 0; k < cnt[i]; ++k) rows[(size_t)t * cap + k] = tag[core[(size_t)k * N + i]];
+            for (int k = 0; k < cnt[i]; ++k) rows[t * cap + k] = tag[core[(size_t)k * N + i]];
         }
         return RBL_OK;
     }
@@ -611,18 +769,18 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
     CK(cudaMemcpy(tab.data(), v.seg_tab, tab.size() * 16, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hcell.data(), v.hcell, 4 * N, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < N; ++i) {
-        int t = tag[i];
+        if (row_of[i] < 0) continue;
+        const size_t t = (size_t)row_of[i];
         counts[t] = cnt[i];
-        int c = cell_index(v, hcell[i]);
         SegCursor cur;
-        cur.init(tab.data() + (size_t)c * v.S);
+        cur.init(tab.data() + (size_t)hcell[i] * v.S);
         int k = 0;
         for (int w = 0; w < v.W && k < cnt[i]; ++w) {
             unsigned word = mask[(size_t)w * N + i];
             while (word) {
                 int bit = __builtin_ctz(word);
                 word &= word - 1u;
-                rows[(size_t)t * cap + k++] = tag[cur.index_of((w << 5) + bit)];
+                rows[t * cap + k++] = tag[cur.index_of((w << 5) + bit)];
             }
         }
     }
@@ -631,11 +789,11 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
 
 rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
 {
-    if (!ctx || !batch || !counts || step < 0 || ctx->view.full_list) return RBL_EINVAL;
+    if (!ctx || !batch || !counts || step < 0) return RBL_EINVAL;
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
     const View &v = ctx->view;
-    size_t N = (size_t)v.N;
+    const size_t N = (size_t)v.N;
     int *dj = (int *)v.staging;
     int *dn = dj + N * (size_t)v.p;
     CK(launch_batch(v, (unsigned long long)step, dj, dn, ctx->stream));
@@ -646,9 +804,11 @@ rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
     CK(cudaMemcpy(jj.data(), dj, 4 * N * (size_t)v.p, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(nb.data(), dn, 4 * N, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < N; ++i) {
-        int t = tag[i];
+        const int2 tl = ctx->h_tile[i >> kTileShift];
+        if ((long long)i >= tl.y) continue;
+        const size_t t = (size_t)ctx->h_box[tl.x].in0 + (size_t)tag[i];
         counts[t] = nb[i];
-        for (int q = 0; q < nb[i]; ++q) batch[(size_t)t * v.p + q] = tag[jj[i * v.p + q]];
+        for (int q = 0; q < nb[i]; ++q) batch[t * v.p + q] = tag[jj[i * v.p + q]];
     }
     return RBL_OK;
 }
@@ -660,20 +820,21 @@ rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist)
         set_err(ctx, "nbins * dr = %g exceeds r_s = %g", (double)nbins * dr, ctx->prm.r_s);
         return RBL_EINVAL;
     }
-    if ((size_t)nbins * 8 > ctx->staging_bytes) {
+    const size_t nh = (size_t)nbins * (size_t)ctx->R;
+    if (nh * 8 > ctx->staging_bytes) {
         set_err(ctx, "too many bins for the staging area");
         return RBL_EINVAL;
     }
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
     unsigned long long *dh = (unsigned long long *)ctx->view.staging;
-    CK(cudaMemsetAsync(dh, 0, 8 * (size_t)nbins, ctx->stream));
+    CK(cudaMemsetAsync(dh, 0, 8 * nh, ctx->stream));
     CK(launch_rdf(ctx->view, dr, nbins, dh, ctx->stream));
-    std::vector<unsigned long long> h(nbins);
-    CK(cudaMemcpyAsync(h.data(), dh, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<unsigned long long> h(nh);
+    CK(cudaMemcpyAsync(h.data(), dh, 8 * nh, cudaMemcpyDeviceToHost, ctx->stream));
     st = check_flags(ctx);
     if (st != RBL_OK) return st;
-    for (int b = 0; b < nbins; ++b) hist[b] += (long long)h[b];
+    for (size_t b = 0; b < nh; ++b) hist[b] += (long long)h[b];
     return RBL_OK;
 }
 
@@ -704,6 +865,10 @@ void rbl_destroy(rbl_ctx *ctx)
     for (int k = 0; k < ctx->ev_cap * 5; ++k) cudaEventDestroy(ctx->ev[k]);
     std::free(ctx->ev);
     delete ctx->h_sc;
+    delete[] ctx->h_rs;
+    delete[] ctx->h_box;
+    delete[] ctx->h_tile;
+    delete[] ctx->h_cell_rep;
     delete ctx;
 }
 
@@ -762,99 +927,32 @@ rbl_status static_scratch_address(void **out)
     *out = g_static_ptr[dev];
     return RBL_OK;
 }
-
-// View over a laid-out region starting at base (same carving as a context's workspace).
-void static_view(View &v, const rbl_params *prm, int N, const Layout &L, char *base)
-{
-    v = View{};
-    v.N = N;
-    v.p = prm->p;
-    v.K = prm->cells_per_cutoff;
-    v.cap_c = L.cap_c;
-    v.W = L.W;
-    v.S = L.S;
-    v.Mcap = L.Mcap;
-    v.full_list = prm->full_list ? 1 : 0;
-    v.precision = prm->precision;
-    v.subtract = prm->subtract_net_force ? 1 : 0;
-    v.ncell = L.ncell;
-    for (int a = 0; a < 3; ++a) {
-        int n = L.n3[a], K = prm->cells_per_cutoff;
-        v.n[a] = n;
-        v.nofs[a] = L.nofs3[a];
-        for (int o = 0; o < L.nofs3[a]; ++o) v.ofs[a][o] = n >= 2 * K + 1 ? o - K : o;
-        v.L[a] = prm->L[a];
-        v.inv[a] = 4294967296.0 / prm->L[a];
-        v.h[a] = (float)(prm->L[a] / 4294967296.0);
-    }
-    for (int sg = 0; sg < L.S; ++sg) {
-        v.seg_oz[sg] = (signed char)(sg / L.nofs3[1]);
-        v.seg_oy[sg] = (signed char)(sg % L.nofs3[1]);
-    }
-    double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
-    double lo = rc - sk > 0.0 ? rc - sk : 0.0;
-    v.t_core_list = (float)((rc + sk) * (rc + sk));
-    v.t_shell_lo = (float)(lo * lo);
-    v.t_cut_list = (float)((rs + sk) * (rs + sk));
-    v.t_rc2 = (float)(rc * rc);
-    v.t_rs2 = (float)(rs * rs);
-    v.t_disp = (float)(0.25 * sk * sk);
-    v.dt = prm->dt;
-    v.T = prm->T;
-    v.gamma = prm->gamma;
-    v.c1 = std::exp(-prm->gamma * prm->dt);
-    v.c2f = (float)std::sqrt((1.0 - v.c1 * v.c1) * prm->T);
-    v.seed = prm->seed;
-    int k = 0;
-    v.x = (double *)(base + L.off[k++]);
-    v.x_alt = (double *)(base + L.off[k++]);
-    v.v = (double *)(base + L.off[k++]);
-    v.v_alt = (double *)(base + L.off[k++]);
-    v.tag = (int *)(base + L.off[k++]);
-    v.tag_alt = (int *)(base + L.off[k++]);
-    v.pos = (int4 *)(base + L.off[k++]);
-    v.pos_alt = (int4 *)(base + L.off[k++]);
-    v.ubuild = (int4 *)(base + L.off[k++]);
-    v.F = (void *)(base + L.off[k++]);
-    v.cell = (int *)(base + L.off[k++]);
-    v.order = (int *)(base + L.off[k++]);
-    v.counts = (int *)(base + L.off[k++]);
-    v.start = (int *)(base + L.off[k++]);
-    v.fill = (int *)(base + L.off[k++]);
-    v.blocksums = (int *)(base + L.off[k++]);
-    v.seg_tab = (int4 *)(base + L.off[k++]);
-    v.core = (int *)(base + L.off[k++]);
-    v.n_core = (int *)(base + L.off[k++]);
-    v.mask = (unsigned *)(base + L.off[k++]);
-    v.n_shell = (int *)(base + L.off[k++]);
-    v.hcell = (int *)(base + L.off[k++]);
-    v.partials = (double *)(base + L.off[k++]);
-    v.sc = (DevScalars *)(base + L.off[k++]);
-    v.staging = (double *)(base + L.off[k++]);
-}
-
 } // namespace
 
 extern "C" rbl_status rbl_forces_static(const rbl_params *prm, int N, const double *x, long long step, double *F,
                                         void *stream)
 {
     if (!x || !F || step < 0) return RBL_EINVAL;
-    rbl_status st = validate(prm, N, nullptr, 0);
+    rbl_status st = validate_batch(prm, 1, &N, nullptr, 0);
     if (st != RBL_OK) return st;
-    const Layout L = make_layout(prm, N);
-    if (L.total > kStaticScratchBytes) return RBL_ENOMEM;
+    const Plan P = make_plan(prm, 1, &N);
+    if (P.total > kStaticScratchBytes) return RBL_ENOMEM;
     void *base = nullptr;
     st = static_scratch_address(&base);
     if (st != RBL_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     View v;
-    static_view(v, prm, N, L, (char *)base);
-    // the array keeps the previous call's contents: reset the scalars this call reads
+    assign_view(v, prm, P, (char *)base);
+    const Box b = make_box(prm, N, 0, 0, 0);
+    // the array keeps the previous call's contents: rewrite the tables and reset the
+    // scalars this call reads
     DevScalars h{};
     h.step = (unsigned long long)step;
+    if (launch_init_single(v, b, s) != cudaSuccess) return RBL_ECUDA;
     if (cudaMemcpyAsync(v.sc, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, s) != cudaSuccess) return RBL_ECUDA;
+    if (cudaMemsetAsync(v.rs, 0, sizeof(RepScalars), s) != cudaSuccess) return RBL_ECUDA;
     if (launch_load_state(v, x, nullptr, s) != cudaSuccess) return RBL_ECUDA;
-    if (launch_rebuild(v, L.ntiles, false, s) != cudaSuccess) return RBL_ECUDA;
+    if (launch_rebuild(v, P.n_scan_blocks, false, s) != cudaSuccess) return RBL_ECUDA;
     if (launch_forces(v, 0, 0, false, s) != cudaSuccess) return RBL_ECUDA;
     if (launch_store_forces(v, F, s) != cudaSuccess) return RBL_ECUDA;
     if (cudaMemcpyAsync(&h, v.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RBL_ECUDA;

@@ -56,9 +56,15 @@ template <bool FP32, bool ENERGY>
 struct Accum {
     float f32[2][3], e32[2], w32[2];   // [0] core, [1] shell (before the batch scale)
     double f64[2][3], e64[2], w64[2];
+    float h[3];                        // the replica's fixed-point unit L / 2^32
+    const double *L;                   // the replica's box (FP64 path)
 
-    __device__ __forceinline__ void zero()
+    __device__ __forceinline__ void zero(const Box &b)
     {
+        h[0] = b.h[0];
+        h[1] = b.h[1];
+        h[2] = b.h[2];
+        L = b.L;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
 #pragma unroll
@@ -80,7 +86,7 @@ struct Accum {
     // Pair (i, j) in region `part` (0 core, 1 shell / full).
     __device__ __forceinline__ void pair(const View &v, int4 pi, int4 pj, int i, int j, int part)
     {
-        PairGeom g = pair_geom(pi, pj, v.h);
+        PairGeom g = pair_geom(pi, pj, h);
         bool inside = in_region(v, g.r2, part);
         if (FP32) {
             float u, w;
@@ -99,7 +105,7 @@ struct Accum {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 double t = v.x[a * N + i] - v.x[a * N + j];
-                t -= v.L[a] * rint(t / v.L[a]);
+                t -= L[a] * rint(t / L[a]);
                 d[a] = t;
             }
             double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -166,11 +172,14 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
     long long qv[3] = {0, 0, 0};
     double f64[3] = {0.0, 0.0, 0.0};
     double e_i = 0.0, w_i = 0.0;
-    if (i < v.N) {
+    bool live = false;
+    const int r = i < v.N ? slot_replica(v, i, live) : 0;
+    if (live) {
+        const Box &b = v.box[r];
         const int4 pi = v.pos[i];
         const int nc = (MODE == 0 || (MODE == 2 && !v.full_list)) ? min(v.n_core[i], v.cap_c) : 0;
         const int ns = v.n_shell[i];
-        const int4 *tab = v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S;
+        const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
         const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
         // stage the mask words (independent loads, in bursts)
         const int nws = min(nwords, kMaskStage);
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
             return w < kMaskStage ? s_mask[w][t] : v.mask[(size_t)w * N + i];
         };
         Accum<FP32, ENERGY> acc;
-        acc.zero();
+        acc.zero(b);
         SegCursor cur;
         cur.init(tab);
         float s32 = 1.0f;
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
             // shell batch: positions in the row -> particle indices
             if constexpr (PMAX > 0) {
                 int S[PMAX];
-                const int nb = batch_sorted<PMAX>(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                const int nb = batch_sorted<PMAX>(b.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
                 if (ns > v.p) {
                     s32 = __fdiv_rn((float)ns, (float)v.p);
                     s64 = (double)ns / (double)v.p;
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                 }
             } else {
                 int S[kMaxP];
-                const int nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                const int nb = floyd_positions(b.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
                 if (ns > v.p) {
                     s32 = __fdiv_rn((float)ns, (float)v.p);
                     s64 = (double)ns / (double)v.p;
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             long long s = warp_sum(qv[a]);
-            if (lane == 0 && s != 0) atomicAdd(&v.sc->fsum_q[a], (unsigned long long)s);
+            if (lane == 0 && s != 0) atomicAdd(&v.rs[r].fsum_q[a], (unsigned long long)s);
         }
         if (ENERGY) {
             double x[2] = {e_i, w_i};
@@ -342,51 +351,54 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
     }
 }
 
-// Reduce the block partials in a fixed order; form the mean force F_cor
-// (Appendix A) and reset the integer accumulator for the next evaluation.
+// One block per replica: reduce its blocks' partials in a fixed order, form its
+// mean force F_cor (Appendix A) and reset its integer accumulator for the next
+// evaluation.  bthreads: threads of the blocks that wrote the partials.
 // exact = 1: store the unsampled energy and virial only (MODE 2 partials).
-__global__ void __launch_bounds__(1024) k_force_finish(View v, int nblk, int fp32, int energy, int subtract,
-                                                       int advance, int exact)
+__global__ void __launch_bounds__(kBlock) k_force_finish(View v, int bthreads, int fp32, int energy, int subtract,
+                                                         int advance, int exact)
 {
-    __shared__ double sh[5][32];
+    __shared__ double sh[5][kBlock / 32];
+    const int r = blockIdx.x;
+    const Box &b = v.box[r];
+    const int b0 = b.first / bthreads, nb = (fp32 && !energy) ? 0 : b.slots / bthreads;
     double acc[5] = {0, 0, 0, 0, 0};
-    if (fp32 && !energy) nblk = 0; // only the integer total is needed
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) acc[k] += v.partials[(size_t)b * 8 + k];
+        for (int q = 0; q < 5; ++q) acc[q] += v.partials[(size_t)(b0 + k) * 8 + q];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        double s = warp_sum(acc[k]);
-        if (lane == 0) sh[k][wid] = s;
+    for (int q = 0; q < 5; ++q) {
+        double s = warp_sum(acc[q]);
+        if (lane == 0) sh[q][wid] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot[5] = {0, 0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int k = 0; k < 5; ++k) tot[k] += sh[k][w];
-        DevScalars *sc = v.sc;
+            for (int q = 0; q < 5; ++q) tot[q] += sh[q][w];
+        RepScalars &rsc = v.rs[r];
         if (exact) {
-            sc->u_exact = tot[3];
-            sc->w_exact = tot[4];
+            rsc.u_exact = tot[3];
+            rsc.w_exact = tot[4];
             return;
         }
         for (int a = 0; a < 3; ++a) {
             double m;
             if (fp32) {
-                long long qs = (long long)sc->fsum_q[a];
-                m = (double)qs * kFixedInv / (double)v.N;
-                sc->fsum_q[a] = 0ull;
+                long long qs = (long long)rsc.fsum_q[a];
+                m = (double)qs * kFixedInv / (double)b.N;
+                rsc.fsum_q[a] = 0ull;
             } else {
-                m = tot[a] / (double)v.N;
+                m = tot[a] / (double)b.N;
             }
-            sc->fcor[a] = subtract ? m : 0.0;
+            rsc.fcor[a] = subtract ? m : 0.0;
         }
         if (energy) {
-            sc->energy = tot[3];
-            sc->virial = tot[4];
+            rsc.energy = tot[3];
+            rsc.virial = tot[4];
         }
-        sc->step += (unsigned long long)advance;
+        if (r == 0) v.sc->step += (unsigned long long)advance;
     }
 }
 
@@ -395,13 +407,16 @@ __global__ void k_store_forces(View v, double *out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
     size_t N = (size_t)v.N;
-    int t = v.tag[i];
+    size_t t = (size_t)v.box[r].in0 + (size_t)v.tag[i];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double f = v.precision == RBL_FP32 ? (double)((const long long *)v.F)[a * N + i] * kFixedInv
                                            : ((const double *)v.F)[a * N + i];
-        out[(size_t)t * 3 + a] = f - v.sc->fcor[a];
+        out[t * 3 + a] = f - v.rs[r].fcor[a];
     }
 }
 
@@ -411,14 +426,20 @@ __global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) {
+        out_n[i] = 0;
+        return;
+    }
     const size_t N = (size_t)v.N;
     const int4 pi = v.pos[i];
     const int ns = v.n_shell[i];
     int S[kMaxP];
-    const int nb = floyd_positions(v.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+    const int nb = floyd_positions(v.box[r].seed, step, pi.w, ns, v.p, S, &v.sc->flags);
     sort_small(S, nb);
     SegCursor cur;
-    cur.init(v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S);
+    cur.init(v.seg_tab + (size_t)v.hcell[i] * v.S);
     int q = 0, seen = 0;
     for (int w = 0; q < nb; ++w) {
         const unsigned word = v.mask[(size_t)w * N + i];
@@ -432,28 +453,34 @@ __global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
     out_n[i] = nb;
 }
 
-// g(r) counts: every pair once per ordered (i, j), classified like the force.
+// g(r) counts: every pair once per ordered (i, j), classified like the force;
+// hist[r][nbins] per replica.
 __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
     const size_t N = (size_t)v.N;
     const int4 pi = v.pos[i];
+    const float h[3] = {v.box[r].h[0], v.box[r].h[1], v.box[r].h[2]};
+    unsigned long long *hr = hist + (size_t)r * nbins;
     auto count = [&](int j, bool core_part) {
-        PairGeom g = pair_geom(pi, v.pos[j], v.h);
+        PairGeom g = pair_geom(pi, v.pos[j], h);
         bool in;
         if (v.full_list) in = g.r2 < v.t_rs2;
         else in = core_part ? g.r2 < v.t_rc2 : (g.r2 >= v.t_rc2 && g.r2 < v.t_rs2);
         if (!in) return;
         float qf = __fdiv_rn(__fsqrt_rn(g.r2), dr);
-        if (qf < (float)nbins) atomicAdd(&hist[(int)qf], 1ull);
+        if (qf < (float)nbins) atomicAdd(&hr[(int)qf], 1ull);
     };
     if (!v.full_list) {
         int nc = min(v.n_core[i], v.cap_c);
         for (int k = 0; k < nc; ++k) count(v.core[(size_t)k * N + i], true);
     }
     SegCursor cur;
-    cur.init(v.seg_tab + (size_t)cell_index(v, v.hcell[i]) * v.S);
+    cur.init(v.seg_tab + (size_t)v.hcell[i] * v.S);
     int left = v.n_shell[i];
     for (int w = 0; left > 0; ++w) {
         unsigned word = v.mask[(size_t)w * N + i];
@@ -495,19 +522,21 @@ cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cud
 
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kForceThreads);
     bool fp32 = v.precision == RBL_FP32;
-    int threads = (fp32 && !energy) ? 32 : 1024;
-    k_force_finish<<<1, threads, 0, s>>>(v, g, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance, 0);
+    int threads = (fp32 && !energy) ? 32 : kBlock;
+    k_force_finish<<<v.R, threads, 0, s>>>(v, kForceThreads, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract,
+                                           advance, 0);
     return cudaGetLastError();
 }
+
+int force_block_threads() { return kForceThreads; }
 
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s)
 {
     int g = ceil_div(v.N, kForceThreads);
     if (v.precision == RBL_FP32) k_force<2, true, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
     else k_force<2, false, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
-    k_force_finish<<<1, 1024, 0, s>>>(v, g, 0, 1, 0, 0, 1);
+    k_force_finish<<<v.R, kBlock, 0, s>>>(v, kForceThreads, 0, 1, 0, 0, 1);
     return cudaGetLastError();
 }
 

@@ -20,58 +20,89 @@ constexpr int kBlock = 256;        // threads per block of the per-particle kern
 constexpr int kMinBlock = 64;      // smallest per-particle block: sizes the per-block partials
 constexpr int kMaxStencil = 7;     // offsets per axis for K <= 3
 
+constexpr int kTile = 256;         // particle slots per tile; every replica starts on a tile
+constexpr int kTileShift = 8;
+static_assert(kBlock == kTile, "a per-particle block covers exactly one tile");
+constexpr int kMaxSeg = kMaxStencil * kMaxStencil;
+
 // Device flags (bit positions in DevScalars::flags).
 enum : unsigned { kFlagOverflow = 1u, kFlagNonFinite = 2u, kFlagCellOverflow = 4u, kFlagRngLimit = 8u };
 
-// Scalars living in device memory (one instance in the workspace).
+// Context-wide scalars living in device memory (one instance in the workspace).
 struct DevScalars {
+    unsigned flags;                 // kFlag* bits
+    int rebuild;                    // 1 when some replica must rebuild before the next force
+    unsigned long long step;        // step counter n (batch/noise counters), shared by all replicas
+};
+
+// Per-replica scalars living in device memory ([R] in the workspace).
+struct RepScalars {
     unsigned long long fsum_q[3];   // FP32 path: sum of fixed-point forces (mod 2^64)
     double fcor[3];                 // mean force subtracted from every particle
     double energy, virial;          // RBL estimates from the last evaluation
     double u_exact, w_exact;        // unsampled energy and virial (on demand)
     double ksum;                    // sum v^2 (on demand)
     double psum[3];                 // sum v (on demand)
-    unsigned flags;                 // kFlag* bits
-    int rebuild;                    // 1 when lists must be rebuilt before the next force
+    int rebuild;                    // 1 when this replica's lists must be rebuilt
     int nc_max, ns_max;             // longest rows at the last build (even past capacity)
     int m_max;                      // largest stencil population at the last build
     unsigned long long ns_sum;      // total shell (or full) entries at the last build
     unsigned long long nc_sum;      // total core entries at the last build
     unsigned long long m_sum;       // sum over particles of their home cell's stencil population
     long long n_rebuild;            // builds so far
-    unsigned long long step;        // step counter n (batch/noise counters)
+};
+
+// One replica: an independent periodic system with its own box, temperature, seed
+// and particle count (a context of one system is a batch of one).  Its particles
+// occupy the slots [first, first + N) and the padding slots up to first + slots
+// (slots = N rounded up to kTile), its cells the range [c0, c0 + ncell) followed by
+// one pad cell that owns the padding slots, so that a single exclusive scan over
+// every replica's cell counts places each replica at its own slots.
+struct Box {
+    double L[3], inv[3];            // inv = 2^32 / L
+    float h[3];                     // L / 2^32 in binary32
+    float c2f;                      // sqrt((1 - c1^2) T) in binary32
+    unsigned long long seed;
+    double T;
+    int N, first, slots, in0;       // particles, first slot, slots, first row in packed caller arrays
+    int c0, ncell;                  // cells [c0, c0 + ncell); c0 + ncell is the pad cell
+    int n[3], nofs[3], ofs[3][kMaxStencil];
+    int S;                          // segments per home cell (nofs_y * nofs_z)
 };
 
 // Kernel-visible view of a context (passed by value).
 //
 // Neighbour storage.  All particles of a home cell share one candidate sequence:
 // the members of the cells of its stencil in canonical order (stencil slots
-// z-major, x-minor; members of a cell in tag order).  Along x the stencil cells of
-// one (y, z) offset are adjacent in memory, so the sequence is S = nofs_y * nofs_z
-// "segments", each one contiguous run of particle indices, or two when it wraps
-// around the periodic x face.  Per home cell, seg_tab[c][s] = (startA, lenA, startB,
-// candidates up to and including segment s): the first piece's start and length,
-// the second piece's start, and the running count (seg_tab[c][S-1].w = M_c).
-// Per particle:
+// z-major, x-minor; members of a cell by x image, then tag).  Along x the stencil
+// cells of one (y, z) offset are adjacent in memory, so the sequence is S_r =
+// nofs_y * nofs_z "segments", each one contiguous run of particle indices, or two
+// when it wraps around the periodic x face.  Per home cell, seg_tab[c][s] =
+// (startA, lenA, startB, candidates up to and including segment s): the first
+// piece's start and length, the second piece's start, and the running count.  Rows
+// are S = max_r S_r entries long; entries past the replica's S_r repeat the total,
+// so seg_tab[c][S-1].w = M_c for every cell.
+// Per particle slot:
 //   core  : explicit list of neighbour indices, column-major core[k][N];
 //   shell : bitmask over the candidate sequence, column-major mask[w][N], bit b of
 //           word w <-> candidate 32 w + b (full list in full_list mode).
 // A shell row in canonical order is the candidate sequence filtered by the mask, so
 // the position of a neighbour in its row is its rank among the set bits.
 struct View {
-    int N, p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
-    int ncell, n[3], nofs[3], ofs[3][kMaxStencil];
-    signed char seg_oy[kMaxStencil * kMaxStencil], seg_oz[kMaxStencil * kMaxStencil]; // row -> (oy, oz) slots
-    double L[3], inv[3];            // inv = 2^32 / L
-    float h[3];                     // L / 2^32 in binary32
+    int N;                          // particle slots of all replicas (stride of per-particle arrays)
+    int R;                          // replicas
+    int ntile;                      // N / kTile
+    int p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
+    int ncell;                      // cells of all replicas, pad cells included
     float t_core_list, t_shell_lo, t_cut_list, t_rc2, t_rs2, t_disp;
-    double dt, T, gamma, c1;
-    float c2f;                      // sqrt((1 - c1^2) T) in binary32
-    unsigned long long seed;
-    // state (cell order); [axis][N] for x and v
+    double dt, gamma, c1;
+    const Box *box;                 // [R]
+    const int2 *tile;               // [ntile]: (replica, end of its live slots)
+    const int *cell_rep;            // [ncell]: replica of each cell
+    // state (cell order within each replica); [axis][N] for x and v
     double *x, *v;                  // current buffer base (3 consecutive N-arrays each)
     double *x_alt, *v_alt;          // other buffer (permutation target)
-    int *tag, *tag_alt;
+    int *tag, *tag_alt;             // tag = particle number within its replica
     int4 *pos, *pos_alt;            // (ux, uy, uz, tag) 32-bit fixed-point image
     int4 *ubuild;                   // image at the last build
     void *F;                        // [3][N]: int64 fixed point (FP32 path) or double
@@ -81,11 +112,20 @@ struct View {
     int *core, *n_core;             // core[k * N + i], k < cap_c
     unsigned *mask;                 // mask[w * N + i], w < W
     int *n_shell;                   // set bits in the mask (N_s, or full-list length)
-    int *hcell;                     // home cell (packed) of each particle at the last build
-    double *partials;               // [nblk][8]
+    int *hcell;                     // home cell (global index) of each particle at the last build
+    double *partials;               // [blocks][8]
+    RepScalars *rs;                 // [R]
     DevScalars *sc;
     double *staging;                // host/device I/O scratch
 };
+
+// Replica of particle slot i (i < N) and whether the slot holds a particle.
+__device__ __forceinline__ int slot_replica(const View &v, int i, bool &live)
+{
+    const int2 t = v.tile[i >> kTileShift];
+    live = i < t.y;
+    return t.x;
+}
 
 // Wrap a cell coordinate into [0, n) for -n <= c < 2n (stencil offsets never
 // reach further): compare-and-add instead of an integer division.
@@ -93,21 +133,6 @@ __host__ __device__ __forceinline__ int wrap_cell(int c, int n)
 {
     c = c >= n ? c - n : c;
     return c < 0 ? c + n : c;
-}
-
-// Home cells are stored packed as cx | cy << 10 | cz << 20 (at most 1024 cells
-// per axis), so no kernel divides to recover the coordinates.
-constexpr int kCellBits = 10;
-__host__ __device__ __forceinline__ int pack_cell(int cx, int cy, int cz)
-{
-    return cx | (cy << kCellBits) | (cz << (2 * kCellBits));
-}
-
-// Linear index of a packed cell.
-__host__ __device__ __forceinline__ int cell_index(const View &v, int packed)
-{
-    const int m = (1 << kCellBits) - 1;
-    return ((packed >> (2 * kCellBits)) * v.n[1] + ((packed >> kCellBits) & m)) * v.n[0] + (packed & m);
 }
 
 // Streams the segments of a home cell in ascending candidate order and maps a
@@ -479,10 +504,11 @@ inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
 
 // Host-side context (C ABI handle).
 struct rbl_ctx {
-    rbl_params prm;
+    rbl_params prm;              // replica 0's parameters (the shared ones are equal for all)
     rbl::View view;
     cudaStream_t stream;
-    int nblk;
+    int R;                       // replicas
+    long long n_real;            // particles of all replicas (rows of the packed caller arrays)
     int n_scan_blocks;
     int lists_valid;   // lists match the current positions
     int force_valid;   // F matches the current positions and step counter
@@ -496,7 +522,11 @@ struct rbl_ctx {
     double phase_ms[4];
     long long phase_steps;
     char err[512];
-    rbl::DevScalars *h_sc; // host mirror of the device scalars
+    rbl::DevScalars *h_sc;      // host mirror of the device scalars
+    rbl::RepScalars *h_rs;      // host mirror of the per-replica scalars [R]
+    rbl::Box *h_box;            // host copy of the replica table [R]
+    int2 *h_tile;               // host copy of the tile table [ntile]
+    int *h_cell_rep;            // host copy of the cell -> replica table [ncell]
 };
 
 // Kernel launchers implemented in the .cu files.
@@ -508,10 +538,12 @@ cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHand
 cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
 cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s);
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s);
+cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s);
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
 cudaError_t launch_kinetic(const View &v, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
+int force_block_threads();
 } // namespace rbl

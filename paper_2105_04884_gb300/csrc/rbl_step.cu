@@ -16,41 +16,57 @@ namespace rbl {
 
 namespace {
 
-// Load AoS tag-ordered x (and v) into the SoA arrays (identity order), wrap x into
-// [0, L), refresh the fixed-point image, and flag non-finite input.
+// Load packed AoS tag-ordered x (and v) into the SoA arrays (identity order within
+// each replica: slot first + t holds tag t), wrap x into [0, L), refresh the
+// fixed-point image, and flag non-finite input.  Padding slots are cleared.
 __global__ void k_load(View v, const double *x, const double *vel)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
     size_t N = (size_t)v.N;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v.x[a * N + i] = v.v[a * N + i] = 0.0;
+        v.tag[i] = 0;
+        v.pos[i] = v.ubuild[i] = make_int4(0, 0, 0, 0);
+        return;
+    }
+    const Box &b = v.box[r];
+    const int t = i - b.first;
+    const size_t row = (size_t)b.in0 + (size_t)t;
     unsigned u[3];
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double xa = x[(size_t)i * 3 + a];
-        double va = vel ? vel[(size_t)i * 3 + a] : 0.0;
+        double xa = x[row * 3 + a];
+        double va = vel ? vel[row * 3 + a] : 0.0;
         bad |= !isfinite(xa) || !isfinite(va);
         if (!isfinite(xa)) xa = 0.0;
-        xa = xa - v.L[a] * floor(xa / v.L[a]);
-        if (xa >= v.L[a]) xa -= v.L[a];
+        xa = xa - b.L[a] * floor(xa / b.L[a]);
+        if (xa >= b.L[a]) xa -= b.L[a];
         if (xa < 0.0) xa = 0.0;
         v.x[a * N + i] = xa;
         v.v[a * N + i] = va;
-        u[a] = quantize(xa, v.inv[a]);
+        u[a] = quantize(xa, b.inv[a]);
     }
-    v.tag[i] = i;
-    v.pos[i] = make_int4((int)u[0], (int)u[1], (int)u[2], i);
+    v.tag[i] = t;
+    v.pos[i] = make_int4((int)u[0], (int)u[1], (int)u[2], t);
     v.ubuild[i] = v.pos[i];
     if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
 }
 
-// SoA cell-ordered state -> AoS tag-ordered output.
+// SoA cell-ordered state -> packed AoS tag-ordered output.
 __global__ void k_store(View v, double *x, double *vel)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
     size_t N = (size_t)v.N;
-    size_t t = (size_t)v.tag[i];
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
+    size_t t = (size_t)v.box[r].in0 + (size_t)v.tag[i];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (x) x[t * 3 + a] = v.x[a * N + i];
@@ -76,63 +92,70 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
+    const Box &b = v.box[r];
     size_t N = (size_t)v.N;
-    const DevScalars *sc = v.sc;
+    const RepScalars *rsc = v.rs + r;
     double vv[3], xx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double f = force_component<FP32>(v, a, i, sc->fcor[a]);
+        double f = force_component<FP32>(v, a, i, rsc->fcor[a]);
         vv[a] = fma(ck, f, v.v[a * N + i]);
     }
     if constexpr (!DRIFT) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) v.v[a * N + i] = vv[a];
-        return;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) xx[a] = v.x[a * N + i];
-    int tag = v.tag[i];
-    if (LANGEVIN) {
-        const double half = 0.5 * v.dt;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) xx[a] = fma(half, vv[a], xx[a]);
-        // O-step noise: Box-Muller of a_k = ((w_k >> 9) + 1/2) 2^-23, stream 1.
-        WordStream ws;
-        ws.init(v.seed, sc->step, (uint32_t)tag, 1u);
-        float av[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) av[k] = __fmul_rn(__fadd_rn((float)(ws.next() >> 9), 0.5f), 1.1920928955078125e-7f);
-        float r0 = sqrtf(-2.0f * logf(av[0]));
-        float r1 = sqrtf(-2.0f * logf(av[2]));
-        float s1, c1v;
-        sincospif(2.0f * av[1], &s1, &c1v);
-        float c3 = cospif(2.0f * av[3]);
-        float xi[3] = {r0 * c1v, r0 * s1, r1 * c3};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double noise = f32_to_double(v.c2f * xi[a]);
-            vv[a] = fma(v.c1, vv[a], noise);
-            xx[a] = fma(half, vv[a], xx[a]);
-        }
     } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) xx[a] = fma(v.dt, vv[a], xx[a]);
-    }
-    unsigned u[3];
-    bool bad = false;
+        for (int a = 0; a < 3; ++a) xx[a] = v.x[a * N + i];
+        int tag = v.tag[i];
+        if (LANGEVIN) {
+            const double half = 0.5 * v.dt;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double xa = wrap(xx[a], v.L[a]);
-        bad |= !finite_bits(xa) || !finite_bits(vv[a]);
-        v.x[a * N + i] = xa;
-        v.v[a * N + i] = vv[a];
-        u[a] = quantize(xa, v.inv[a]);
+            for (int a = 0; a < 3; ++a) xx[a] = fma(half, vv[a], xx[a]);
+            // O-step noise: Box-Muller of a_k = ((w_k >> 9) + 1/2) 2^-23, stream 1.
+            WordStream ws;
+            ws.init(b.seed, v.sc->step, (uint32_t)tag, 1u);
+            float av[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) av[k] = __fmul_rn(__fadd_rn((float)(ws.next() >> 9), 0.5f), 1.1920928955078125e-7f);
+            float r0 = sqrtf(-2.0f * logf(av[0]));
+            float r1 = sqrtf(-2.0f * logf(av[2]));
+            float s1, c1v;
+            sincospif(2.0f * av[1], &s1, &c1v);
+            float c3 = cospif(2.0f * av[3]);
+            float xi[3] = {r0 * c1v, r0 * s1, r1 * c3};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double noise = f32_to_double(b.c2f * xi[a]);
+                vv[a] = fma(v.c1, vv[a], noise);
+                xx[a] = fma(half, vv[a], xx[a]);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) xx[a] = fma(v.dt, vv[a], xx[a]);
+        }
+        unsigned u[3];
+        bool bad = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double xa = wrap(xx[a], b.L[a]);
+            bad |= !finite_bits(xa) || !finite_bits(vv[a]);
+            v.x[a * N + i] = xa;
+            v.v[a * N + i] = vv[a];
+            u[a] = quantize(xa, b.inv[a]);
+        }
+        int4 np = make_int4((int)u[0], (int)u[1], (int)u[2], tag);
+        v.pos[i] = np;
+        PairGeom g = pair_geom(np, v.ubuild[i], b.h);
+        if (g.r2 > v.t_disp) {
+            v.rs[r].rebuild = 1;
+            v.sc->rebuild = 1;
+        }
+        if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
     }
-    int4 np = make_int4((int)u[0], (int)u[1], (int)u[2], tag);
-    v.pos[i] = np;
-    PairGeom g = pair_geom(np, v.ubuild[i], v.h);
-    if (g.r2 > v.t_disp) v.sc->rebuild = 1;
-    if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
 }
 
 template <typename T>
@@ -143,7 +166,8 @@ __device__ __forceinline__ T wsum(T x)
     return x;
 }
 
-// sum v^2 and sum v: per-block partials (fixed order), then one block.
+// sum v^2 and sum v: per-block (= per-tile) partials in a fixed order, then one
+// block per replica.  Padding slots hold v = 0.
 __global__ void __launch_bounds__(kBlock) k_kinetic(View v)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
@@ -172,13 +196,15 @@ __global__ void __launch_bounds__(kBlock) k_kinetic(View v)
     }
 }
 
-__global__ void __launch_bounds__(1024) k_kinetic_finish(View v, int nblk)
+__global__ void __launch_bounds__(kBlock) k_kinetic_finish(View v)
 {
-    __shared__ double sh[4][32];
+    __shared__ double sh[4][kBlock / 32];
+    const Box &bx = v.box[blockIdx.x];
+    const int t0 = bx.first >> kTileShift, nt = bx.slots >> kTileShift;
     double acc[4] = {0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int b = threadIdx.x; b < nt; b += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += v.staging[(size_t)b * 4 + k];
+        for (int k = 0; k < 4; ++k) acc[k] += v.staging[(size_t)(t0 + b) * 4 + k];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -190,12 +216,31 @@ __global__ void __launch_bounds__(1024) k_kinetic_finish(View v, int nblk)
         double tot[4] = {0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int k = 0; k < 4; ++k) tot[k] += sh[k][w];
-        v.sc->ksum = tot[0];
-        for (int a = 0; a < 3; ++a) v.sc->psum[a] = tot[1 + a];
+        RepScalars &rsc = v.rs[blockIdx.x];
+        rsc.ksum = tot[0];
+        for (int a = 0; a < 3; ++a) rsc.psum[a] = tot[1 + a];
     }
 }
 
+// Replica tables of a context of one system, written on the device so that a
+// caller that may not allocate host memory can set them up (replica 0 owns every
+// tile and cell).
+__global__ void k_init_single(View v, Box b)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) *const_cast<Box *>(v.box) = b;
+    if (k < v.ntile) const_cast<int2 *>(v.tile)[k] = make_int2(0, b.first + b.N);
+    if (k < v.ncell) const_cast<int *>(v.cell_rep)[k] = 0;
+}
+
 } // namespace
+
+cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s)
+{
+    int n = v.ntile > v.ncell ? v.ntile : v.ncell;
+    k_init_single<<<ceil_div(n, kBlock), kBlock, 0, s>>>(v, b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s)
 {
@@ -231,7 +276,7 @@ cudaError_t launch_kinetic(const View &v, cudaStream_t s)
 {
     int g = ceil_div(v.N, kBlock);
     k_kinetic<<<g, kBlock, 0, s>>>(v);
-    k_kinetic_finish<<<1, 1024, 0, s>>>(v, g);
+    k_kinetic_finish<<<v.R, kBlock, 0, s>>>(v);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,9 @@ is no fallback path.
 
     sys = System(x, v, L, r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005, T=1.5, gamma=1.0)
     sys.step(100); obs = sys.observables(); F = sys.forces()
+
+    ens = Ensemble([Replica(x0, v0, L0, T0, seed0), ...], r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005)
+    ens.step(100); obs = ens.observables()  # one dict per replica
 """
 from __future__ import annotations
 
@@ -49,7 +52,8 @@ class rbl_obs(ctypes.Structure):
         return d
 
 
-EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_create", "rbl_set_state", "rbl_get_state",
+EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
+           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state",
            "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists",
            "rbl_get_batch",
            "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_forces_static", "rbl_destroy",
@@ -78,12 +82,16 @@ def load(build_if_missing: bool = False):
     L.rbl_params_default.restype = None
     L.rbl_workspace_size.argtypes = [ctypes.POINTER(rbl_params), I, ctypes.POINTER(ctypes.c_size_t)]
     L.rbl_create.argtypes = [ctypes.POINTER(rbl_params), I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    L.rbl_workspace_size_batch.argtypes = [ctypes.POINTER(rbl_params), I, P, ctypes.POINTER(ctypes.c_size_t)]
+    L.rbl_create_batch.argtypes = [ctypes.POINTER(rbl_params), I, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    L.rbl_replicas.argtypes = [P]
     L.rbl_set_state.argtypes = [P, P, P, LL, I]
     L.rbl_get_state.argtypes = [P, P, P, ctypes.POINTER(LL), I]
     L.rbl_build_lists.argtypes = [P]
     L.rbl_forces.argtypes = [P, P, I]
     L.rbl_step.argtypes = [P, I]
     L.rbl_observables.argtypes = [P, ctypes.POINTER(rbl_obs)]
+    L.rbl_exact_energy.argtypes = [P, P, P]
     L.rbl_get_lists.argtypes = [P, I, P, I, P]
     L.rbl_get_batch.argtypes = [P, LL, P, P]
     L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
@@ -128,38 +136,39 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-class System:
-    """One RBL (or full-list) system on the current CUDA device and stream."""
+class _Context:
+    """A librbl context on one CUDA device and a stream of its own; R replicas whose
+    particle rows are packed one replica after another."""
 
-    def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
-                 full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
-                 stream=None, device=None):
+    def _create(self, prms, Ns, stream, device):
         import torch
 
         self._torch = torch
         self.lib = load()
-        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
-        self.N = int(x.shape[0])
-        self.prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
-                               cells_per_cutoff, cap_core, cap_stencil)
+        self.R = len(prms)
+        self.Ns = [int(n) for n in Ns]
+        self.N = int(sum(self.Ns))
+        self.prm = prms[0]
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         # a stream of its own (the legacy default stream cannot host graph replays)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        arr = (rbl_params * self.R)(*prms)
+        nn = (ctypes.c_int * self.R)(*self.Ns)
         size = ctypes.c_size_t()
-        self._check(self.lib.rbl_workspace_size(ctypes.byref(self.prm), self.N, ctypes.byref(size)))
+        self.h = None
+        self._check(self.lib.rbl_workspace_size_batch(arr, self.R, nn, ctypes.byref(size)))
         self.workspace = torch.empty(int(size.value) + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         aligned = (base + 255) & ~255
         h = ctypes.c_void_p()
-        st = self.lib.rbl_create(ctypes.byref(self.prm), self.N, ctypes.c_void_p(aligned), int(size.value),
-                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        st = self.lib.rbl_create_batch(arr, self.R, nn, ctypes.c_void_p(aligned), int(size.value),
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         self.h = h
         if st != 0:
             msg = self.lib.rbl_last_error(h).decode() if h else ""
             self.lib.rbl_destroy(h)
             self.h = None
             raise RblError(st, msg)
-        self.set_state(x, v, step)
 
     # -- plumbing
     def _check(self, st):
@@ -220,21 +229,20 @@ class System:
     def step(self, n=1):
         self._check(self.lib.rbl_step(self.h, int(n)))
 
-    def observables(self) -> dict:
-        o = rbl_obs()
-        self._check(self.lib.rbl_observables(self.h, ctypes.byref(o)))
-        return o.as_dict()
+    def _observables(self):
+        o = (rbl_obs * self.R)()
+        self._check(self.lib.rbl_observables(self.h, o))
+        return [o[r].as_dict() for r in range(self.R)]
 
-    def exact_energy(self):
-        """(U, W): unsampled energy and virial sums over all pairs with r < r_s."""
-        U = ctypes.c_double()
-        W = ctypes.c_double()
-        self._check(self.lib.rbl_exact_energy(self.h, ctypes.byref(U), ctypes.byref(W)))
-        return U.value, W.value
+    def _exact_energy(self):
+        U = np.zeros(self.R)
+        W = np.zeros(self.R)
+        self._check(self.lib.rbl_exact_energy(self.h, _ptr(U), _ptr(W)))
+        return U, W
 
     def get_lists(self, kind, cap=None):
         if cap is None:
-            cap = int(self.observables()["Nc_max" if kind == 0 else "Ns_max"]) + 1
+            cap = max(int(o["Nc_max" if kind == 0 else "Ns_max"]) for o in self._observables()) + 1
         rows = np.full((self.N, cap), -1, np.int32)
         counts = np.zeros(self.N, np.int32)
         self._check(self.lib.rbl_get_lists(self.h, int(kind), _ptr(rows), int(cap), _ptr(counts)))
@@ -257,8 +265,72 @@ class System:
         self._check(self.lib.rbl_phase_times(self.h, ms, ctypes.byref(n), int(bool(reset))))
         return list(ms), n.value
 
+    def _rdf(self, dr, nbins, hist):
+        self._check(self.lib.rbl_rdf(self.h, float(dr), int(nbins), _ptr(hist)))
+        return hist
+
+
+class System(_Context):
+    """One RBL (or full-list) system on the current CUDA device and stream."""
+
+    def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
+                 full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
+                 stream=None, device=None):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
+        prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
+                          cells_per_cutoff, cap_core, cap_stencil)
+        self._create([prm], [int(x.shape[0])], stream, device)
+        self.set_state(x, v, step)
+
+    def observables(self) -> dict:
+        return self._observables()[0]
+
+    def exact_energy(self):
+        """(U, W): unsampled energy and virial sums over all pairs with r < r_s."""
+        U, W = self._exact_energy()
+        return float(U[0]), float(W[0])
+
     def rdf(self, dr, nbins, hist=None):
         if hist is None:
             hist = np.zeros(nbins, np.int64)
-        self._check(self.lib.rbl_rdf(self.h, float(dr), int(nbins), _ptr(hist)))
-        return hist
+        return self._rdf(dr, nbins, hist)
+
+
+class Replica:
+    """One member of an ensemble: its state, box, bath temperature and seed."""
+
+    def __init__(self, x, v, L, T, seed):
+        self.x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        self.v = None if v is None else np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        self.L, self.T, self.seed = L, T, seed
+
+
+class Ensemble(_Context):
+    """R independent replicas (own N, box, T and seed; shared radii, p, dt, gamma,
+    precision) advanced together: one launch per kernel for all of them."""
+
+    def __init__(self, replicas, r_c, r_s, skin, p, dt, gamma=0.0, precision=RBL_FP32, full_list=False,
+                 subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0, stream=None,
+                 device=None):
+        prms = [make_params(rp.L, r_c, r_s, skin, p, dt, rp.T, gamma, rp.seed, precision, full_list,
+                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil) for rp in replicas]
+        self._create(prms, [len(rp.x) for rp in replicas], stream, device)
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ns)])
+        x = np.concatenate([rp.x for rp in replicas])
+        v = np.concatenate([rp.v if rp.v is not None else np.zeros_like(rp.x) for rp in replicas])
+        self.set_state(x, v, step)
+
+    def split(self, a):
+        """Packed per-particle rows -> list of per-replica arrays."""
+        return [a[self.offsets[r]:self.offsets[r + 1]] for r in range(self.R)]
+
+    def observables(self) -> list:
+        return self._observables()
+
+    def exact_energy(self):
+        return self._exact_energy()
+
+    def rdf(self, dr, nbins, hist=None):
+        if hist is None:
+            hist = np.zeros((self.R, nbins), np.int64)
+        return self._rdf(dr, nbins, hist)

@@ -89,3 +89,29 @@ def test_product_has_no_oracle_dependency():
                     text = open(os.path.join(dirpath, f)).read()
                     assert "import oracle" not in text and "from oracle" not in text, f
                     assert "rbl_oracle" not in text, f
+
+
+def test_batch_validation(lib):
+    """Replicas may differ in box, temperature, seed and N only."""
+    def size(prms, Ns):
+        arr = (rbl.rbl_params * len(prms))(*prms)
+        nn = (ctypes.c_int * len(Ns))(*Ns)
+        s = ctypes.c_size_t()
+        return lib.rbl_workspace_size_batch(arr, len(prms), nn, ctypes.byref(s)), s.value
+
+    a = rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005, T=1.5, seed=1)
+    b = rbl.make_params([12.0, 12.5, 13.0], 1.5, 3.5, 0.3, 10, 0.005, T=1.1, seed=7)
+    st, n2 = size([a, b], [1000, 1500])
+    assert st == 0
+    st1, n1 = size([a], [1000])
+    assert st1 == 0 and n2 > n1
+    assert size([a, b], [1000, 1])[0] == 1                              # N < 2 in one replica
+    for field, val in (("r_c", 1.2), ("p", 5), ("dt", 0.002), ("precision", rbl.RBL_FP64),
+                       ("full_list", 1), ("cells_per_cutoff", 1), ("gamma", 1.0)):
+        c = rbl.make_params([12.0] * 3, 1.5, 3.5, 0.3, 10, 0.005)
+        setattr(c, field, val)
+        assert size([a, c], [1000, 1000])[0] == 1, field
+    h = ctypes.c_void_p()
+    assert lib.rbl_create_batch(None, 0, None, None, 0, None, ctypes.byref(h)) == 1
+    lib.rbl_destroy(h)
+    assert lib.rbl_replicas(None) == 0

@@ -18,7 +18,7 @@ if not torch.cuda.is_available():
 import bench  # noqa: E402
 from paper_2105_04884_gb300 import rbl  # noqa: E402
 
-CFG = dict(bench.PHYS, steps=6000, discard=2000)
+CFG = dict(bench.PHYS)  # 10^4 steps, first 2000 discarded, 16 blocks of 500
 
 
 @pytest.fixture(scope="module")
