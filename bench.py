@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-physics", action="store_true", help="skip the matched-physics block")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
+    ap.add_argument("--ensemble-steps", type=int, default=200)
     ap.add_argument("--physics", action="store_true",
                     help="run the full matched-physics sweep (r_c x p x precision vs the full list) instead")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="override particle count (debug only)")
@@ -238,6 +240,50 @@ def physics_compare(a, b, dr):
                 "peak_full": [float(b["g"][ib]), float(b["g_err"][ib]), (ib + 0.5) * dr],
                 "max_abs_diff": float(np.max(np.abs(a["g"] - b["g"])))}
     return res
+
+
+ENSEMBLE = dict(R=256, rc=1.5, rs=3.5, skin=0.3, p=10, dt=0.005, gamma=1.0, K=2)
+
+
+def ensemble_bench(a, rank, timed):
+    """Batched ensemble: 256 replicas, N log-uniform in [500, 20000], rho* in
+    [0.6, 0.9], T* in [1, 2], FP32, one launch per kernel for all replicas and one
+    graph per step; beside it the same replicas as 256 separate contexts stepped
+    one after another (the unbatched alternative, fewer steps)."""
+    import torch
+
+    from paper_2105_04884_gb300 import inputs, rbl
+
+    e = ENSEMBLE
+    reps = inputs.ensemble(e["R"], seed=1 + rank)
+    shared = dict(r_c=e["rc"], r_s=e["rs"], skin=e["skin"], p=e["p"], dt=e["dt"], gamma=e["gamma"],
+                  cells_per_cutoff=e["K"], precision=rbl.RBL_FP32)
+    ntot = sum(rp.N for rp in reps)
+    ens = rbl.Ensemble(reps, **shared)
+    ens.step(a.warmup)
+    K = a.ensemble_steps
+    ms, _ = timed(ens, K, phases=False)
+    obs = ens.observables()
+    del ens
+    torch.cuda.empty_cache()
+    # unbatched: one context per replica, each stepped k times in turn
+    k = max(3, K // 10)
+    singles = [rbl.System(rp.x, rp.v, rp.L, T=rp.T, seed=rp.seed, **shared) for rp in reps]
+    for s1 in singles:
+        s1.step(a.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s1 in singles:
+        s1.step(k)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    del singles
+    torch.cuda.empty_cache()
+    return {"workload": "lj_ensemble_R256_N500-20000_rho0.6-0.9_T1-2_rc1.5_rs3.5_p10_nvt", "replicas": e["R"],
+            "particles": ntot, "steps": K, "value": ntot * K / (ms * 1e-3), "unit": "particle-steps/s",
+            "ms_per_step": ms / K, "rebuilds_per_replica_mean": sum(o["n_rebuild"] for o in obs) / e["R"],
+            "separate_contexts": {"value": ntot * k / t_single, "steps": k,
+                                  "ms_per_step": t_single * 1e3 / k}}
 
 
 def physics_inputs(seed=1, cfg=PHYS):
@@ -448,6 +494,8 @@ def run_ours(a, rank, world, local):
                          "d2h_bytes_per_step": 48 * N / a.steps + 256,
                          "path": "rbl_set_state(host) + steps x (rbl_step(1) + rbl_observables) + rbl_get_state(host)"}
         del se
+    if not a.no_ensemble:
+        result["ensemble"] = ensemble_bench(a, rank, timed)
     if rank == 0 and not a.no_physics:
         # the bench workload's (r_c, p) and r_c = 2.0 (the matched setting), each
         # against one full-list trajectory

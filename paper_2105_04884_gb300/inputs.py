@@ -9,9 +9,11 @@ sigma = epsilon = m = 1, periodic cubic box), widened to the sizes the library i
 benchmarked at:
 
 * ``fcc(N, rho, ...)``: face-centred cubic start, n = ceil((N/4)^(1/3)) unit cells a
-  side, sites in lexicographic (ix, iy, iz, basis) order, the first N kept, lattice
-  constant a = L/n with L = (N/rho)^(1/3), shifted by a/4 off the box faces, plus a
-  uniform jitter of half-width ``jitter`` per coordinate.
+  side, sites in lexicographic (ix, iy, iz, basis) order; when N < 4 n^3 the sites
+  floor(k 4 n^3 / N), k = 0..N-1, are kept (evenly spread, so the start has the
+  nominal density everywhere); lattice constant a = L/n with L = (N/rho)^(1/3),
+  shifted by a/4 off the box faces, plus a uniform jitter of half-width ``jitter``
+  per coordinate.
 * ``maxwell_boltzmann(N, T, ...)``: N(0, sqrt(T)) components, mean removed, rescaled to
   exactly T with 3N - 3 degrees of freedom.
 * ``slab(...)``: liquid FCC slab over the central fraction of z plus a uniform vapour.
@@ -44,7 +46,9 @@ def fcc(N: int, rho: float, jitter: float = 0.01, seed: int = 1, L=None) -> tupl
     basis = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
     ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
-    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)[:N]
+    sites = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    keep = (np.arange(N, dtype=np.int64) * sites.shape[0]) // N  # evenly spread subset
+    sites = sites[keep]
     x = (sites + 0.25) * a
     if jitter > 0:
         x = x + _rng(seed, 2).uniform(-jitter, jitter, size=x.shape)
