@@ -317,8 +317,14 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int co
     __syncwarp();
     const int M = pre[S];
     int4 *gt = v.seg_tab + (size_t)c * v.S;
-    for (int sg = lane; sg < v.S; sg += 32)
-        gt[sg] = sg < S ? make_int4(sA[sg], lA[sg], sB[sg], pre[sg + 1]) : make_int4(0, 0, 0, M);
+    for (int sg = lane; sg < v.S; sg += 32) {
+        if (sg < S) {
+            const int split = pre[sg] + lA[sg];
+            gt[sg] = make_int4(sA[sg] - pre[sg], split, sB[sg] - split, pre[sg + 1]);
+        } else {
+            gt[sg] = make_int4(0, M, 0, M);
+        }
+    }
     const int s0 = v.start[c], s1 = v.start[c + 1];
     if (s1 == s0) return;
     // the masks index this cell's candidate sequence: remember the cell until the

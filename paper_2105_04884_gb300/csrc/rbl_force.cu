@@ -165,6 +165,7 @@ template <int MODE, bool FP32, bool ENERGY, int PMAX>
 __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset)
 {
     __shared__ unsigned s_mask[kMaskStage][kForceThreads];
+    __shared__ unsigned short s_pref[kMaskStage][kForceThreads]; // set bits before each staged word
     const unsigned long long step = v.sc->step + (unsigned long long)step_offset;
     const int t = threadIdx.x;
     const int i = blockIdx.x * kForceThreads + t;
@@ -181,15 +182,21 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
         const int ns = v.n_shell[i];
         const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
         const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
-        // stage the mask words (independent loads, in bursts)
+        // stage the mask words (independent loads, in bursts) and their running
+        // popcounts
         const int nws = min(nwords, kMaskStage);
+        int run = 0;
         for (int w0 = 0; w0 < nws; w0 += 8) {
             unsigned tmp[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) tmp[u] = w0 + u < nws ? v.mask[(size_t)(w0 + u) * N + i] : 0u;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (w0 + u < nws) s_mask[w0 + u][t] = tmp[u];
+                if (w0 + u < nws) {
+                    s_mask[w0 + u][t] = tmp[u];
+                    s_pref[w0 + u][t] = (unsigned short)run;
+                    run += __popc(tmp[u]);
+                }
         }
         auto mask_word = [&](int w) -> unsigned {
             return w < kMaskStage ? s_mask[w][t] : v.mask[(size_t)w * N + i];
@@ -210,20 +217,55 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
                     s64 = (double)ns / (double)v.p;
                 }
                 int J[PMAX];
-                int w = 0, seen = 0;
-                unsigned word = nb > 0 ? mask_word(0) : 0u;
-                int cnt = __popc(word);
+                if (nwords <= kMaskStage) {
+                    // Each drawn rank is resolved on its own, with no branch: the word
+                    // holding it by a binary search over the staged running popcounts,
+                    // the bit by select_bit, the particle by a binary search over the
+                    // segment table's running counts.  PMAX equals p (or bounds it), so
+                    // the PMAX independent chains overlap; a data-dependent walk along
+                    // the row would diverge across the warp and serialise them.  Slots
+                    // past the batch resolve a clamped rank and are not used.
+                    const int S_ = v.S;
+                    const int top = S_ <= 32 ? 16 : 32;
 #pragma unroll
-                for (int q = 0; q < PMAX; ++q) {
-                    J[q] = i;
-                    if (q < nb) {
-                        const int tq = S[q];
-                        while (tq >= seen + cnt) {
-                            seen += cnt;
-                            word = mask_word(++w);
-                            cnt = __popc(word);
+                    for (int q = 0; q < PMAX; ++q) {
+                        const int tq = min(S[q], max(ns - 1, 0));
+                        int w = 0;
+#pragma unroll
+                        for (int sw = kMaskStage / 2; sw >= 1; sw >>= 1) {
+                            const int mid = w + sw;
+                            const int pm = (int)s_pref[min(mid, kMaskStage - 1)][t];
+                            w = (mid < nws && pm <= tq) ? mid : w;
                         }
-                        J[q] = cur.index_of((w << 5) + select_bit(word, tq - seen));
+                        const int cand = (w << 5) + select_bit(s_mask[w][t], tq - (int)s_pref[w][t]);
+                        int sg = 0;
+#pragma unroll
+                        for (int sw = 32; sw >= 1; sw >>= 1) {
+                            if (sw > top) continue;
+                            const int m2 = sg + sw;
+                            const int end = __ldg(&tab[min(m2, S_) - 1].w);
+                            sg = (m2 <= S_ && end <= cand) ? m2 : sg;
+                        }
+                        const int4 e = __ldg(&tab[min(sg, S_ - 1)]);
+                        J[q] = cand < e.y ? e.x + cand : e.z + cand;
+                    }
+                } else {
+                    // rows longer than the staging area: walk the row in order
+                    int w = 0, seen = 0;
+                    unsigned word = nb > 0 ? mask_word(0) : 0u;
+                    int cnt = __popc(word);
+#pragma unroll
+                    for (int q = 0; q < PMAX; ++q) {
+                        J[q] = i;
+                        if (q < nb) {
+                            const int tq = S[q];
+                            while (tq >= seen + cnt) {
+                                seen += cnt;
+                                word = mask_word(++w);
+                                cnt = __popc(word);
+                            }
+                            J[q] = cur.index_of((w << 5) + select_bit(word, tq - seen));
+                        }
                     }
                 }
 #pragma unroll
@@ -502,9 +544,20 @@ cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s)
     if constexpr (MODE == 1) {
         k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
     } else {
-        if (v.p > 32) k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
-        else if (v.p <= 16) k_force<MODE, FP32, ENERGY, 16><<<g, kForceThreads, 0, s>>>(v, step_offset);
-        else k_force<MODE, FP32, ENERGY, 32><<<g, kForceThreads, 0, s>>>(v, step_offset);
+        // every rank slot up to PMAX is resolved, so PMAX is p itself for the usual
+        // batch sizes and a bound otherwise
+        switch (v.p) {
+        case 1: k_force<MODE, FP32, ENERGY, 1><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        case 2: k_force<MODE, FP32, ENERGY, 2><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        case 5: k_force<MODE, FP32, ENERGY, 5><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        case 10: k_force<MODE, FP32, ENERGY, 10><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        case 20: k_force<MODE, FP32, ENERGY, 20><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        default:
+            if (v.p <= 8) k_force<MODE, FP32, ENERGY, 8><<<g, kForceThreads, 0, s>>>(v, step_offset);
+            else if (v.p <= 16) k_force<MODE, FP32, ENERGY, 16><<<g, kForceThreads, 0, s>>>(v, step_offset);
+            else if (v.p <= 32) k_force<MODE, FP32, ENERGY, 32><<<g, kForceThreads, 0, s>>>(v, step_offset);
+            else k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
+        }
     }
     return cudaGetLastError();
 }

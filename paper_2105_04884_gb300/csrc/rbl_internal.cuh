@@ -77,10 +77,11 @@ struct Box {
 // z-major, x-minor; members of a cell by x image, then tag).  Along x the stencil
 // cells of one (y, z) offset are adjacent in memory, so the sequence is S_r =
 // nofs_y * nofs_z "segments", each one contiguous run of particle indices, or two
-// when it wraps around the periodic x face.  Per home cell, seg_tab[c][s] =
-// (startA, lenA, startB, candidates up to and including segment s): the first
-// piece's start and length, the second piece's start, and the running count.  Rows
-// are S = max_r S_r entries long; entries past the replica's S_r repeat the total,
+// when it wraps around the periodic x face.  With pre_s the candidates before
+// segment s and A, B its pieces, seg_tab[c][s] = (startA - pre_s, pre_s + lenA,
+// startB - pre_s - lenA, pre_s + lenA + lenB): candidate k of the segment is particle
+// k < .y ? .x + k : .z + k, and .w is the running count through the segment.  Rows
+// are S = max_r S_r entries long; entries past the replica's S_r are (0, M_c, 0, M_c),
 // so seg_tab[c][S-1].w = M_c for every cell.
 // Per particle slot:
 //   core  : explicit list of neighbour indices, column-major core[k][N];
@@ -140,25 +141,19 @@ __host__ __device__ __forceinline__ int wrap_cell(int c, int n)
 struct SegCursor {
     const int4 *tab;      // seg_tab row of the home cell
     int seg;              // current segment
-    int pre;              // candidates before the current segment
-    int4 e;               // (startA, lenA, startB, candidates through the segment)
+    int4 e;               // its table entry
 
     __host__ __device__ __forceinline__ void init(const int4 *tabp)
     {
         tab = tabp;
         seg = 0;
-        pre = 0;
         e = tab[0];
     }
     // cand must not decrease between calls.
     __host__ __device__ __forceinline__ int index_of(int cand)
     {
-        while (cand >= e.w) {
-            pre = e.w;
-            e = tab[++seg];
-        }
-        int off = cand - pre;
-        return off < e.y ? e.x + off : e.z + (off - e.y);
+        while (cand >= e.w) e = tab[++seg];
+        return cand < e.y ? e.x + cand : e.z + cand;
     }
 };
 
