@@ -181,6 +181,12 @@ rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W);
  * longer than cap return RBL_EOVERFLOW. Builds lists if stale. */
 rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts);
 
+/* The same rows for m selected particles only: which[m] are packed row indices,
+ * rows[m][cap] and counts[m] receive their rows as rbl_get_lists would.  Copies
+ * only those particles' list data, so it suits very large systems.  Builds lists
+ * if stale; host pointers. */
+rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, int *rows, int cap, int *counts);
+
 /* The batch B(i) the force would use at step counter `step` with the current
  * lists: batch[N][p] neighbour tags in ascending row position, counts[N] = min(p,
  * N_s); host pointers. */

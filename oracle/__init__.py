@@ -79,6 +79,8 @@ def _declare(L):
     L.orc_lj.argtypes = [I, P, P, P]
     L.orc_rbl_forces.argtypes = [I, P, P, D, D, D, I, U64, U64, P, P, I, P, P, I, P, P, P, P]
     L.orc_rbl_forces.restype = I
+    L.orc_sample.argtypes = [I, P, P, D, D, D, I, I, U64, U64, I, P, I, I, P, P, P, P, P, P, P]
+    L.orc_sample.restype = I
     L.orc_full_forces.argtypes = [I, P, P, D, P, P, I, P, P]
     L.orc_full_forces.restype = I
     L.orc_brute_forces.argtypes = [I, P, P, D, P, P]
@@ -226,6 +228,40 @@ def rbl_forces(x, L, rc, rs, skin, p, seed, step, lists, want_batch=False):
                          lists.core.shape[1], _p(lists.shell), _p(lists.n_shell), lists.shell.shape[1], _p(F),
                          _p(ev), _p(batch), _p(bn))
     return F, ev, batch, bn
+
+
+class Sample:
+    """Rows, batches and forces of sampled particles (see sample())."""
+
+    def __init__(self, idx, core, n_core, shell, n_shell, batch, n_batch, F):
+        self.idx = idx
+        self.core, self.n_core, self.shell, self.n_shell = core, n_core, shell, n_shell
+        self.batch, self.n_batch, self.F = batch, n_batch, F
+
+    def row(self, kind, k):
+        arr, cnt = getattr(self, kind), getattr(self, "n_" + kind)
+        return arr[k, : cnt[k]]
+
+
+def sample(x, L, rc, rs, skin, p, seed, step, idx, K=2, cap_core=160, cap_shell=640):
+    """Core and shell rows (canonical order), batch at `step` and un-subtracted RBL
+    force of the particles idx, each computed on its own against all the others."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    m = idx.shape[0]
+    core = np.full((m, cap_core), -1, np.int32)
+    shell = np.full((m, cap_shell), -1, np.int32)
+    nc = np.zeros(m, np.int32)
+    ns = np.zeros(m, np.int32)
+    batch = np.full((m, max(p, 1)), -1, np.int32)
+    nb = np.zeros(m, np.int32)
+    F = np.zeros((m, 3))
+    st = lib().orc_sample(n, _p(x), _p(_f64(L)), rc, rs, skin, K, p, seed, step, m, _p(idx), cap_core, cap_shell,
+                          _p(core), _p(nc), _p(shell), _p(ns), _p(batch), _p(nb), _p(F))
+    if st != 0:
+        raise OverflowError("oracle row exceeded its capacity")
+    return Sample(idx, core, nc, shell, ns, batch, nb, F)
 
 
 def full_forces(x, L, rs, lists):

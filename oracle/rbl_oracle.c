@@ -585,6 +585,47 @@ void orc_lj(int n, const double *r, double *u_out, double *fmag_out)
  * batch_out (optional, stride p): the chosen shell entries (tags), in position
  * order; batch_n: their number.                                               */
 /* ------------------------------------------------------------------------- */
+/* RBL force on particle i from its core row and shell row (Eqs. (3)-(4)):
+ * F_i = sum over the core row of f_ij for r < r_c, plus s times the sum over the
+ * batch B(i) of f_ij for r_c <= r < r_s, s = N_s/p when N_s > p (else 1); the batch
+ * is the Floyd sample of row positions drawn from Philox stream 0 of (seed, step,
+ * tag i).  Also returns this particle's halves of the energy and virial estimates. */
+static void force_one(int i, const double *x, const uint32_t *u, const fixed_frame *f, const thresholds *t,
+                      const double L[3], int p, uint64_t seed, uint64_t step, const int32_t *crow, int nc,
+                      const int32_t *srow, int ns, int32_t *pos, double Fi[3], double *e_i, double *w_i,
+                      int32_t *batch_out, int32_t *batch_n)
+{
+    double fc[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
+    double ec = 0.0, es = 0.0, wc = 0.0, wsum = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        int j = crow[k];
+        float r2f = pair_r2f(u + 3 * i, u + 3 * j, f->h);
+        if (!(r2f < t->rc2)) continue;
+        double d[3], fv[3], vir;
+        min_image(x + 3 * i, x + 3 * j, L, d);
+        ec += lj_pair(d, fv, &vir);
+        wc += vir;
+        for (int a = 0; a < 3; ++a) fc[a] += fv[a];
+    }
+    int nb = orc_batch_positions(seed, step, (uint32_t)i, ns, p, pos);
+    double s = ns > p ? (double)ns / (double)p : 1.0;
+    for (int b = 0; b < nb; ++b) {
+        int j = srow[pos[b]];
+        if (batch_out) batch_out[b] = j;
+        float r2f = pair_r2f(u + 3 * i, u + 3 * j, f->h);
+        if (!(r2f >= t->rc2 && r2f < t->rs2)) continue;
+        double d[3], fv[3], vir;
+        min_image(x + 3 * i, x + 3 * j, L, d);
+        es += lj_pair(d, fv, &vir);
+        wsum += vir;
+        for (int a = 0; a < 3; ++a) fs[a] += fv[a];
+    }
+    if (batch_n) *batch_n = nb;
+    for (int a = 0; a < 3; ++a) Fi[a] = fc[a] + s * fs[a];
+    *e_i = 0.5 * (ec + s * es);
+    *w_i = 0.5 * (wc + s * wsum);
+}
+
 int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double rs, double skin, int p,
                    uint64_t seed, uint64_t step, const int32_t *core, const int32_t *n_core, int cap_core,
                    const int32_t *shell, const int32_t *n_shell, int cap_shell, double *F, double *energy_virial,
@@ -602,38 +643,12 @@ int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double 
         int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p > 0 ? p : 1));
 #pragma omp for schedule(static)
         for (int i = 0; i < n; ++i) {
-            double fc[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
-            double ec = 0.0, es = 0.0, wc = 0.0, wsum = 0.0;
-            const int32_t *crow = core + (size_t)i * cap_core;
-            for (int k = 0; k < n_core[i]; ++k) {
-                int j = crow[k];
-                float r2f = pair_r2f(u + 3 * i, u + 3 * j, f.h);
-                if (!(r2f < t.rc2)) continue;
-                double d[3], fv[3], vir;
-                min_image(x + 3 * i, x + 3 * j, L, d);
-                ec += lj_pair(d, fv, &vir);
-                wc += vir;
-                for (int a = 0; a < 3; ++a) fc[a] += fv[a];
-            }
-            int ns = n_shell[i];
-            int nb = orc_batch_positions(seed, step, (uint32_t)i, ns, p, pos);
-            double s = ns > p ? (double)ns / (double)p : 1.0;
-            const int32_t *srow = shell + (size_t)i * cap_shell;
-            for (int b = 0; b < nb; ++b) {
-                int j = srow[pos[b]];
-                if (batch_out) batch_out[(size_t)i * p + b] = j;
-                float r2f = pair_r2f(u + 3 * i, u + 3 * j, f.h);
-                if (!(r2f >= t.rc2 && r2f < t.rs2)) continue;
-                double d[3], fv[3], vir;
-                min_image(x + 3 * i, x + 3 * j, L, d);
-                es += lj_pair(d, fv, &vir);
-                wsum += vir;
-                for (int a = 0; a < 3; ++a) fs[a] += fv[a];
-            }
-            if (batch_n) batch_n[i] = nb;
-            for (int a = 0; a < 3; ++a) F[3 * i + a] = fc[a] + s * fs[a];
-            e_tot += 0.5 * (ec + s * es);
-            w_tot += 0.5 * (wc + s * wsum);
+            double e_i, w_i;
+            force_one(i, x, u, &f, &t, L, p, seed, step, core + (size_t)i * cap_core, n_core[i],
+                      shell + (size_t)i * cap_shell, n_shell[i], pos, F + 3 * (size_t)i, &e_i, &w_i,
+                      batch_out ? batch_out + (size_t)i * p : NULL, batch_n ? batch_n + i : NULL);
+            e_tot += e_i;
+            w_tot += w_i;
         }
         free(pos);
     }
@@ -643,6 +658,73 @@ int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double 
     }
     free(u);
     return ORC_OK;
+}
+
+/* Rows, batch and force of m sampled particles idx[0..m) of a large system, each
+ * computed on its own: the core and shell rows by testing every other particle
+ * (the definition, as in orc_build_lists_brute) and sorting them into the
+ * canonical order, the batch and the force as in orc_rbl_forces (no mean
+ * subtraction: that needs every particle).  Rows at stride cap_core / cap_shell,
+ * batches at stride p, forces [m][3].  For checking a large system particle by
+ * particle.                                                                     */
+int orc_sample(int n, const double *x, const double L[3], double rc, double rs, double skin, int K, int p,
+               uint64_t seed, uint64_t step, int m, const int32_t *idx, int cap_core, int cap_shell,
+               int32_t *core, int32_t *n_core, int32_t *shell, int32_t *n_shell, int32_t *batch,
+               int32_t *n_batch, double *F)
+{
+    fixed_frame f;
+    frame_init(&f, L);
+    thresholds t = make_thresholds(rc, rs, skin);
+    cell_grid g;
+    grid_init(&g, L, rs + skin, K);
+    uint32_t *u = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)n);
+    int *cells3 = (int *)malloc(sizeof(int) * 3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) u[3 * i + a] = quantize1(x[3 * i + a], f.inv[a]);
+        cell_of(&g, u + 3 * i, cells3 + 3 * i);
+    }
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        int maxcap = cap_core > cap_shell ? cap_core : cap_shell;
+        row_key *scratch = (row_key *)malloc(sizeof(row_key) * (size_t)(maxcap + 1));
+        int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p > 0 ? p : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < m; ++k) {
+            const int i = idx[k];
+            int32_t *crow = core + (size_t)k * cap_core, *srow = shell + (size_t)k * cap_shell;
+            int nc = 0, ns = 0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                float r2 = pair_r2f(u + 3 * i, u + 3 * j, f.h);
+                if (r2 < t.core_list) {
+                    if (nc < cap_core) crow[nc] = j;
+                    ++nc;
+                }
+                if (r2 >= t.shell_lo && r2 < t.cut_list) {
+                    if (ns < cap_shell) srow[ns] = j;
+                    ++ns;
+                }
+            }
+            n_core[k] = nc;
+            n_shell[k] = ns;
+            if (nc > cap_core || ns > cap_shell) {
+#pragma omp atomic write
+                status = ORC_EOVERFLOW;
+                continue;
+            }
+            sort_row(crow, nc, &g, cells3, u, i, scratch);
+            sort_row(srow, ns, &g, cells3, u, i, scratch);
+            double e_i, w_i;
+            force_one(i, x, u, &f, &t, L, p, seed, step, crow, nc, srow, ns, pos, F + 3 * (size_t)k, &e_i,
+                      &w_i, batch + (size_t)k * p, n_batch + k);
+        }
+        free(pos);
+        free(scratch);
+    }
+    free(u);
+    free(cells3);
+    return status;
 }
 
 /* Classical cutoff force from a full Verlet list: sum over full_i with

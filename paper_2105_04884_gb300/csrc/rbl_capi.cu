@@ -787,6 +787,69 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
     return RBL_OK;
 }
 
+rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, int *rows, int cap, int *counts)
+{
+    if (!ctx || !which || !rows || !counts || (kind != 0 && kind != 1) || m < 0 || cap < 1) return RBL_EINVAL;
+    if (kind == 0 && ctx->view.full_list) return RBL_EINVAL;
+    for (int k = 0; k < m; ++k)
+        if (which[k] < 0 || which[k] >= ctx->n_real) {
+            set_err(ctx, "row %lld out of range", which[k]);
+            return RBL_EINVAL;
+        }
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    const View &v = ctx->view;
+    const size_t N = (size_t)v.N;
+    std::vector<int> tag(N);
+    CK(cudaMemcpy(tag.data(), v.tag, 4 * N, cudaMemcpyDeviceToHost));
+    // slot of every requested packed row
+    std::vector<long long> slot_of((size_t)ctx->n_real, -1);
+    for (size_t i = 0; i < N; ++i) {
+        const int2 t = ctx->h_tile[i >> kTileShift];
+        if ((long long)i < t.y) slot_of[(size_t)ctx->h_box[t.x].in0 + (size_t)tag[i]] = (long long)i;
+    }
+    std::vector<unsigned> words((size_t)v.W);
+    std::vector<int> entries((size_t)v.cap_c);
+    std::vector<int4> tab((size_t)v.S);
+    for (int k = 0; k < m; ++k) {
+        const size_t i = (size_t)slot_of[(size_t)which[k]];
+        int cnt = 0;
+        CK(cudaMemcpy(&cnt, (kind == 0 ? v.n_core : v.n_shell) + i, 4, cudaMemcpyDeviceToHost));
+        if (cnt > cap) {
+            set_err(ctx, "row %lld has %d entries, more than cap %d", which[k], cnt, cap);
+            return RBL_EOVERFLOW;
+        }
+        counts[k] = cnt;
+        int *out = rows + (size_t)k * cap;
+        if (kind == 0) {
+            // column i of core[cap_c][N]
+            const int nc = cnt < v.cap_c ? cnt : v.cap_c;
+            if (nc > 0)
+                CK(cudaMemcpy2D(entries.data(), 4, v.core + i, 4 * N, 4, (size_t)nc, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < nc; ++q) out[q] = tag[entries[q]];
+            continue;
+        }
+        int hc = 0;
+        CK(cudaMemcpy(&hc, v.hcell + i, 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tab.data(), v.seg_tab + (size_t)hc * v.S, 16 * (size_t)v.S, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy2D(words.data(), 4, v.mask + i, 4 * N, 4, (size_t)v.W, cudaMemcpyDeviceToHost));
+        SegCursor cur;
+        cur.init(tab.data());
+        int q = 0;
+        for (int w = 0; w < v.W && q < cnt; ++w) {
+            unsigned word = words[w];
+            while (word) {
+                int bit = __builtin_ctz(word);
+                word &= word - 1u;
+                out[q++] = tag[cur.index_of((w << 5) + bit)];
+            }
+        }
+    }
+    return RBL_OK;
+}
+
 rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
 {
     if (!ctx || !batch || !counts || step < 0) return RBL_EINVAL;

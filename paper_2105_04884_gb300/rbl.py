@@ -54,7 +54,7 @@ class rbl_obs(ctypes.Structure):
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
            "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state",
-           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists",
+           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
            "rbl_get_batch",
            "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_forces_static", "rbl_destroy",
            "rbl_last_error", "rbl_status_string"]
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False):
     L.rbl_observables.argtypes = [P, ctypes.POINTER(rbl_obs)]
     L.rbl_exact_energy.argtypes = [P, P, P]
     L.rbl_get_lists.argtypes = [P, I, P, I, P]
+    L.rbl_get_rows.argtypes = [P, I, P, I, P, I, P]
     L.rbl_get_batch.argtypes = [P, LL, P, P]
     L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
     L.rbl_set_phase_timing.argtypes = [P, I]
@@ -246,6 +247,17 @@ class _Context:
         rows = np.full((self.N, cap), -1, np.int32)
         counts = np.zeros(self.N, np.int32)
         self._check(self.lib.rbl_get_lists(self.h, int(kind), _ptr(rows), int(cap), _ptr(counts)))
+        return rows, counts
+
+    def get_rows(self, kind, which, cap=None):
+        """Rows of the particles `which` (packed row indices) only."""
+        which = np.ascontiguousarray(which, dtype=np.int64)
+        if cap is None:
+            cap = max(int(o["Nc_max" if kind == 0 else "Ns_max"]) for o in self._observables()) + 1
+        rows = np.full((len(which), cap), -1, np.int32)
+        counts = np.zeros(len(which), np.int32)
+        self._check(self.lib.rbl_get_rows(self.h, int(kind), _ptr(which), len(which), _ptr(rows), int(cap),
+                                          _ptr(counts)))
         return rows, counts
 
     def get_batch(self, step):

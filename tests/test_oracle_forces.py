@@ -151,3 +151,20 @@ def test_shell_estimator_unbiased_and_srswor_variance(rs_, skin_):
         # variance ratio: sampling error of a variance estimate ~ sqrt(2/M) (plus kurtosis)
         assert np.all(np.abs(emp / var - 1) < 0.25), (i, emp / var)
     assert zmax < 4.5
+
+
+def test_sample_equals_full_system_oracle():
+    """Per-particle sampling (rows by testing all pairs, batch, force) reproduces the
+    whole-system oracle exactly for the sampled particles."""
+    rc, rs, skin, p, seed, step = 1.5, 3.5, 0.3, 10, 7, 13
+    x, L = inputs.fcc(1500, 0.8, 0.2, seed=21)
+    lists = oracle.build_lists(x, L, rc, rs, skin, K=2)
+    F, _, batch, bn = oracle.rbl_forces(x, L, rc, rs, skin, p, seed, step, lists, want_batch=True)
+    idx = np.array([0, 1, 17, 512, 777, 1499])
+    smp = oracle.sample(x, L, rc, rs, skin, p, seed, step, idx, K=2)
+    for k, i in enumerate(idx):
+        assert np.array_equal(smp.row("core", k), lists.row("core", i))
+        assert np.array_equal(smp.row("shell", k), lists.row("shell", i))
+        assert smp.n_batch[k] == bn[i]
+        assert np.array_equal(smp.batch[k, : bn[i]], batch[i, : bn[i]])
+        assert np.array_equal(smp.F[k], F[i])
