@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-physics", action="store_true", help="skip the matched-physics block")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
+    ap.add_argument("--no-slab", action="store_true", help="skip the liquid-vapour slab block")
     ap.add_argument("--ensemble-steps", type=int, default=200)
     ap.add_argument("--physics", action="store_true",
                     help="run the full matched-physics sweep (r_c x p x precision vs the full list) instead")
@@ -286,6 +287,59 @@ def ensemble_bench(a, rank, timed):
                                   "ms_per_step": t_single * 1e3 / k}}
 
 
+SLAB = dict(N=4194304, rho_l=0.75, rho_v=0.01, frac=0.4, T=0.9, rc=1.5, rs=4.0, skin=0.3, p=20, dt=0.005,
+            gamma=1.0, K=2, steps=500, dz=0.5)
+
+
+def slab_bench(a, rank, timed):
+    """Liquid-vapour slab: N = 4,194,304 in Lx = Ly, Lz = 4 Lx, liquid rho* = 0.75
+    over the central 40% of z, vapour 0.01 elsewhere, T* = 0.9, r_c = 1.5, r_s = 4.0,
+    p = 20, FP32; 500 steps of RBL and of the full list from the same start, then
+    the z density profile (0.5 sigma bins) of both, averaged over 5 more samples
+    10 steps apart."""
+    import numpy as np
+    import torch
+
+    from paper_2105_04884_gb300 import inputs, rbl
+
+    c = SLAB
+    V = c["N"] / (c["rho_l"] * c["frac"] + c["rho_v"] * (1.0 - c["frac"]))
+    Lx = (V / 4.0) ** (1.0 / 3.0)
+    x, L = inputs.slab(c["N"], Lx, 4.0 * Lx, c["rho_l"], c["rho_v"], c["frac"], seed=1 + rank)
+    v = inputs.maxwell_boltzmann(len(x), c["T"], seed=1 + rank)
+    nb = int(round(L[2] / c["dz"]))
+    common = dict(r_c=c["rc"], r_s=c["rs"], skin=c["skin"], p=c["p"], dt=c["dt"], T=c["T"], gamma=c["gamma"],
+                  seed=1 + rank, cells_per_cutoff=c["K"], precision=rbl.RBL_FP32, rho_cap=c["rho_l"])
+    out = {"workload": "lj_slab_N4194304_rhoL0.75_rhoV0.01_T0.9_rc1.5_rs4.0_p20_nvt", "N": len(x),
+           "box": [float(L[0]), float(L[1]), float(L[2])], "steps": c["steps"]}
+    prof = {}
+    for name, full in (("rbl", False), ("full_list", True)):
+        s = rbl.System(x, v, L, full_list=full, **common)
+        ms, _ = timed(s, c["steps"], phases=False)
+        h = np.zeros(nb, np.int64)
+        for _ in range(5):
+            s.step(10)
+            s.density_profile(2, nb, h)
+        prof[name] = h / 5.0 / (L[0] * L[1] * c["dz"])
+        out[name] = {"value": len(x) * c["steps"] / (ms * 1e-3), "unit": "particle-steps/s",
+                     "ms_per_step": ms / c["steps"], "T_kin": s.observables()["T_kin"]}
+        del s
+        torch.cuda.empty_cache()
+    z = (np.arange(nb) + 0.5) * c["dz"]
+    liquid = np.abs(z - L[2] / 2) < 0.3 * c["frac"] * L[2]
+    vapour = np.abs(z - L[2] / 2) > (0.5 * c["frac"] + 0.1) * L[2]
+    for name in prof:
+        out[name]["rho_liquid"] = float(prof[name][liquid].mean())
+        out[name]["rho_vapour"] = float(prof[name][vapour].mean())
+    # per-bin difference in units of the bins' counting noise (Poisson, both runs)
+    cnt = L[0] * L[1] * c["dz"] * 5.0
+    sig = np.sqrt((prof["rbl"] + prof["full_list"]) / cnt + 1e-12)
+    out["profile_max_abs_diff"] = float(np.max(np.abs(prof["rbl"] - prof["full_list"])))
+    out["profile_rms_z"] = float(np.sqrt(np.mean(((prof["rbl"] - prof["full_list"]) / sig) ** 2)))
+    out["speedup_vs_full_list"] = out["rbl"]["value"] / out["full_list"]["value"]
+    return out
+
+
 def physics_inputs(seed=1, cfg=PHYS):
     from paper_2105_04884_gb300 import inputs
 
@@ -496,6 +550,8 @@ def run_ours(a, rank, world, local):
         del se
     if not a.no_ensemble:
         result["ensemble"] = ensemble_bench(a, rank, timed)
+    if not a.no_slab:
+        result["slab"] = slab_bench(a, rank, timed)
     if rank == 0 and not a.no_physics:
         # the bench workload's (r_c, p) and r_c = 2.0 (the matched setting), each
         # against one full-list trajectory

@@ -81,6 +81,10 @@ typedef struct {
     int cap_core;         /* core row capacity; 0 = derived from the density */
     int cap_stencil;      /* largest stencil population of a cell (shell/full rows are
                              bitmasks over it); 0 = derived from the density */
+    double rho_cap;       /* number density the derived capacities are sized for;
+                             0 = the mean density N/V.  Set it to the densest
+                             region's density for inhomogeneous systems (a liquid
+                             slab in vapour), else rows overflow (RBL_EOVERFLOW). */
 } rbl_params;
 
 typedef struct {
@@ -199,6 +203,14 @@ rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts);
  * nbins * dr <= r_s.  hist[R][nbins] int64 (one histogram per replica), host
  * pointer, accumulated (not cleared).  Builds lists if stale. */
 rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
+
+/* Density profile along axis (0 = x, 1 = y, 2 = z) at the current positions
+ * (Sec. 3 observables; the slab benchmark's z profile): adds to hist[r][b] the
+ * number of particles of replica r with floor(u_a nbins / 2^32) = b, u_a the
+ * particle's 32-bit fixed-point image along the axis (bins of width L_a / nbins).
+ * 1 <= nbins <= 12288.  hist[R][nbins] int64, host pointer, accumulated (not
+ * cleared).  Synchronises. */
+rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *hist);
 
 /* Phase timing.  While enabled, rbl_step launches each step's phases directly (no
  * graph replay) and brackets them with CUDA events on the context's stream:

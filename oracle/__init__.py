@@ -90,6 +90,7 @@ def _declare(L):
     L.orc_tail.argtypes = [D, D, P]
     L.orc_thermo.argtypes = [I, P, P, D, P]
     L.orc_rdf_counts.argtypes = [I, P, P, F, I, P]
+    L.orc_density_profile.argtypes = [I, P, P, I, I, P]
 
 
 def _p(a):
@@ -332,3 +333,11 @@ def rdf_counts(x, L, dr, nbins):
     h = np.zeros(nbins, np.int64)
     lib().orc_rdf_counts(x.shape[0], _p(x), _p(_f64(L)), dr, nbins, _p(h))
     return h
+
+
+def density_profile(x, L, axis, nbins):
+    """Particle counts in nbins equal slabs along axis (fixed-point binning)."""
+    x = _f64(x, (-1, 3))
+    hist = np.zeros(nbins, np.int64)
+    lib().orc_density_profile(x.shape[0], _p(x), _p(_f64(L)), int(axis), int(nbins), _p(hist))
+    return hist

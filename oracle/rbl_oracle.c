@@ -1024,3 +1024,18 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Density profile along one axis (Sec. 3 observables): particle counts in nbins
+ * slabs of equal width; particle i goes to bin floor(u_a nbins / 2^32), u_a its
+ * 32-bit fixed-point image (the rule that assigns cells).  hist accumulated.    */
+/* ------------------------------------------------------------------------- */
+void orc_density_profile(int n, const double *x, const double L[3], int axis, int nbins, int64_t *hist)
+{
+    fixed_frame f;
+    frame_init(&f, L);
+    for (int i = 0; i < n; ++i) {
+        uint32_t u = quantize1(x[3 * i + axis], f.inv[axis]);
+        hist[(int)(((uint64_t)u * (uint64_t)nbins) >> 32)] += 1;
+    }
+}

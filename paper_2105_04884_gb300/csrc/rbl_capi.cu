@@ -66,7 +66,7 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
 {
     if (!p) BAD("params is NULL");
     if (N < 2) BAD("N must be >= 2 (got %d)", N);
-    const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma};
+    const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma, p->rho_cap};
     for (double v : vals)
         if (!std::isfinite(v)) BAD("non-finite parameter");
     if (!(p->r_c > 0.0 && p->r_c < p->r_s)) BAD("need 0 < r_c < r_s (got r_c=%g, r_s=%g)", p->r_c, p->r_s);
@@ -79,7 +79,7 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
     for (int a = 0; a < 3; ++a)
         if (!(p->L[a] >= 2.0 * (p->r_s + p->skin)))
             BAD("box length L[%d]=%g is below 2 (r_s + skin) = %g", a, p->L[a], 2.0 * (p->r_s + p->skin));
-    if (p->cap_core < 0 || p->cap_stencil < 0) BAD("capacities must be >= 0");
+    if (p->cap_core < 0 || p->cap_stencil < 0 || !(p->rho_cap >= 0.0)) BAD("capacities must be >= 0");
     double cells = 1.0;
     for (int a = 0; a < 3; ++a) cells *= std::floor(p->L[a] * p->cells_per_cutoff / (p->r_s + p->skin));
     if (cells > (double)(1 << 28)) BAD("box too large: %.0f cells", cells);
@@ -98,7 +98,7 @@ rbl_status validate_batch(const rbl_params *prm, int R, const int *N, char *err,
         if (a.r_c != b.r_c || a.r_s != b.r_s || a.skin != b.skin || a.p != b.p || a.dt != b.dt ||
             a.gamma != b.gamma || a.precision != b.precision || a.full_list != b.full_list ||
             a.subtract_net_force != b.subtract_net_force || a.cells_per_cutoff != b.cells_per_cutoff ||
-            a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil)
+            a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil || a.rho_cap != b.rho_cap)
             BAD("replica %d differs from replica 0 in a shared parameter (only L, T, seed may differ)", r);
         slots += round_up_ll(N[r], kTile);
     }
@@ -110,7 +110,7 @@ rbl_status validate_batch(const rbl_params *prm, int R, const int *N, char *err,
 Geo replica_geo(const rbl_params *p, int N)
 {
     Geo g{};
-    const double rho = N / (p->L[0] * p->L[1] * p->L[2]);
+    const double rho = p->rho_cap > 0.0 ? p->rho_cap : N / (p->L[0] * p->L[1] * p->L[2]);
     const double rcut = p->r_s + p->skin;
     const int K = p->cells_per_cutoff;
     long long nc = 1;
@@ -896,6 +896,25 @@ rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist)
     std::vector<unsigned long long> h(nh);
     CK(cudaMemcpyAsync(h.data(), dh, 8 * nh, cudaMemcpyDeviceToHost, ctx->stream));
     st = check_flags(ctx);
+    if (st != RBL_OK) return st;
+    for (size_t b = 0; b < nh; ++b) hist[b] += (long long)h[b];
+    return RBL_OK;
+}
+
+rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *hist)
+{
+    if (!ctx || !hist || axis < 0 || axis > 2 || nbins < 1 || nbins > kMaxProfileBins) return RBL_EINVAL;
+    const size_t nh = (size_t)nbins * (size_t)ctx->R;
+    if (nh * 8 > ctx->staging_bytes) {
+        set_err(ctx, "too many bins for the staging area");
+        return RBL_EINVAL;
+    }
+    unsigned long long *dh = (unsigned long long *)ctx->view.staging;
+    CK(cudaMemsetAsync(dh, 0, 8 * nh, ctx->stream));
+    CK(launch_profile(ctx->view, axis, nbins, dh, ctx->stream));
+    std::vector<unsigned long long> h(nh);
+    CK(cudaMemcpyAsync(h.data(), dh, 8 * nh, cudaMemcpyDeviceToHost, ctx->stream));
+    rbl_status st = check_flags(ctx);
     if (st != RBL_OK) return st;
     for (size_t b = 0; b < nh; ++b) hist[b] += (long long)h[b];
     return RBL_OK;

@@ -540,5 +540,7 @@ cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t 
 cudaError_t launch_kinetic(const View &v, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
+cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);
+constexpr int kMaxProfileBins = 12288; // shared-memory histogram of one block
 int force_block_threads();
 } // namespace rbl

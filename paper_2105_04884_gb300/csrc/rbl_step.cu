@@ -222,6 +222,29 @@ __global__ void __launch_bounds__(kBlock) k_kinetic_finish(View v)
     }
 }
 
+// Density profile along one axis (Sec. 3 observables): particle counts in nbins
+// slabs of equal width, bin = floor(u_a nbins / 2^32) from the fixed-point image
+// (exact, and the same rule that assigns cells).  Shared-memory histogram per
+// block (a block lies in one replica), then one global add per bin; hist[R][nbins].
+__global__ void k_profile(View v, int axis, int nbins, unsigned long long *hist)
+{
+    extern __shared__ unsigned s_hist[];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) s_hist[b] = 0u;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool live = false;
+    const int r = i < v.N ? slot_replica(v, i, live) : v.tile[(v.N - 1) >> kTileShift].x;
+    if (live) {
+        const int4 p = v.pos[i];
+        const unsigned u = axis == 0 ? (unsigned)p.x : (axis == 1 ? (unsigned)p.y : (unsigned)p.z);
+        atomicAdd(&s_hist[(int)(((unsigned long long)u * (unsigned)nbins) >> 32)], 1u);
+    }
+    __syncthreads();
+    unsigned long long *hr = hist + (size_t)r * nbins;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (s_hist[b]) atomicAdd(&hr[b], (unsigned long long)s_hist[b]);
+}
+
 // Replica tables of a context of one system, written on the device so that a
 // caller that may not allocate host memory can set them up (replica 0 owns every
 // tile and cell).
@@ -234,6 +257,12 @@ __global__ void k_init_single(View v, Box b)
 }
 
 } // namespace
+
+cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s)
+{
+    k_profile<<<ceil_div(v.N, kBlock), kBlock, (size_t)nbins * 4, s>>>(v, axis, nbins, hist);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s)
 {

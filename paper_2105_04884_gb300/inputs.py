@@ -73,11 +73,12 @@ def uniform_gas(N: int, L, seed: int = 1) -> np.ndarray:
 
 def slab(N: int, Lx: float, Lz: float, rho_liquid: float, rho_vapour: float, frac: float = 0.4,
          seed: int = 1, min_sep: float = 0.9) -> tuple[np.ndarray, np.ndarray]:
-    """Liquid FCC slab over |z - Lz/2| < frac Lz / 2, uniform vapour elsewhere.
+    """Liquid FCC slab over |z - Lz/2| < frac Lz / 2, vapour elsewhere.
 
-    The liquid lattice constant gives density rho_liquid; vapour particles are placed
-    uniformly, rejecting any closer than min_sep (in z-distance bins) to the slab faces.
-    The first N particles are kept (liquid first).
+    The liquid lattice constant gives density rho_liquid.  Vapour particles are a
+    random subset of a simple cubic lattice of spacing 1.2 sigma (so no two start
+    closer than 1 sigma), kept min_sep away from the slab faces.  The first N
+    particles are kept (liquid first).
     """
     L = np.array([Lx, Lx, Lz], dtype=np.float64)
     a = (4.0 / rho_liquid) ** (1.0 / 3.0)
@@ -96,10 +97,14 @@ def slab(N: int, Lx: float, Lz: float, rho_liquid: float, rho_vapour: float, fra
     n_vap = max(0, N - liquid.shape[0])
     vap = np.zeros((0, 3))
     if n_vap:
-        cand = rng.uniform(0.0, 1.0, size=(4 * n_vap + 64, 3)) * L
-        zc = cand[:, 2]
-        keep = (zc < z_lo - min_sep) | (zc > z_hi + min_sep)
-        vap = cand[keep][:n_vap]
+        sp = 1.2
+        gx = (np.arange(int(Lx / sp)) + 0.5) * (Lx / int(Lx / sp))
+        gz = (np.arange(int(Lz / sp)) + 0.5) * (Lz / int(Lz / sp))
+        gz = gz[(gz < z_lo - min_sep) | (gz > z_hi + min_sep)]
+        gxx, gyy, gzz = np.meshgrid(gx, gx, gz, indexing="ij")
+        grid = np.stack([gxx.ravel(), gyy.ravel(), gzz.ravel()], axis=1)
+        pick = rng.choice(grid.shape[0], size=min(n_vap, grid.shape[0]), replace=False)
+        vap = grid[np.sort(pick)] + rng.uniform(-0.1, 0.1, size=(len(pick), 3))
     x = np.concatenate([liquid, vap])[:N]
     x = np.mod(x, L)
     return np.ascontiguousarray(x), L

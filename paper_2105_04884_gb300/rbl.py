@@ -35,7 +35,8 @@ class rbl_params(ctypes.Structure):
                 ("skin", ctypes.c_double), ("p", ctypes.c_int), ("dt", ctypes.c_double), ("T", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int),
                 ("full_list", ctypes.c_int), ("subtract_net_force", ctypes.c_int),
-                ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_stencil", ctypes.c_int)]
+                ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_stencil", ctypes.c_int),
+                ("rho_cap", ctypes.c_double)]
 
 
 class rbl_obs(ctypes.Structure):
@@ -53,11 +54,10 @@ class rbl_obs(ctypes.Structure):
 
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
-           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state",
-           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
-           "rbl_get_batch",
-           "rbl_rdf", "rbl_set_phase_timing", "rbl_phase_times", "rbl_forces_static", "rbl_destroy",
-           "rbl_last_error", "rbl_status_string"]
+           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state", "rbl_build_lists",
+           "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
+           "rbl_get_batch", "rbl_rdf", "rbl_density_profile", "rbl_set_phase_timing", "rbl_phase_times",
+           "rbl_forces_static", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = False):
     L.rbl_get_rows.argtypes = [P, I, P, I, P, I, P]
     L.rbl_get_batch.argtypes = [P, LL, P, P]
     L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
+    L.rbl_density_profile.argtypes = [P, I, I, P]
     L.rbl_set_phase_timing.argtypes = [P, I]
     L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
     L.rbl_forces_static.argtypes = [ctypes.POINTER(rbl_params), I, P, LL, P, P]
@@ -113,7 +114,7 @@ def load(build_if_missing: bool = False):
 
 
 def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32, full_list=False,
-                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0) -> rbl_params:
+                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, rho_cap=0.0) -> rbl_params:
     prm = rbl_params()
     load().rbl_params_default(ctypes.byref(prm))
     Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
@@ -126,6 +127,7 @@ def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RB
     prm.subtract_net_force = int(bool(subtract_net_force))
     prm.cells_per_cutoff = int(cells_per_cutoff)
     prm.cap_core, prm.cap_stencil = int(cap_core), int(cap_stencil)
+    prm.rho_cap = float(rho_cap)
     return prm
 
 
@@ -277,6 +279,10 @@ class _Context:
         self._check(self.lib.rbl_phase_times(self.h, ms, ctypes.byref(n), int(bool(reset))))
         return list(ms), n.value
 
+    def _profile(self, axis, nbins, hist):
+        self._check(self.lib.rbl_density_profile(self.h, int(axis), int(nbins), _ptr(hist)))
+        return hist
+
     def _rdf(self, dr, nbins, hist):
         self._check(self.lib.rbl_rdf(self.h, float(dr), int(nbins), _ptr(hist)))
         return hist
@@ -287,10 +293,10 @@ class System(_Context):
 
     def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
                  full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
-                 stream=None, device=None):
+                 stream=None, device=None, rho_cap=0.0):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
         prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
-                          cells_per_cutoff, cap_core, cap_stencil)
+                          cells_per_cutoff, cap_core, cap_stencil, rho_cap)
         self._create([prm], [int(x.shape[0])], stream, device)
         self.set_state(x, v, step)
 
@@ -306,6 +312,12 @@ class System(_Context):
         if hist is None:
             hist = np.zeros(nbins, np.int64)
         return self._rdf(dr, nbins, hist)
+
+    def density_profile(self, axis, nbins, hist=None):
+        """Particle counts in nbins equal slabs along axis."""
+        if hist is None:
+            hist = np.zeros(nbins, np.int64)
+        return self._profile(axis, nbins, hist)
 
 
 class Replica:
@@ -323,9 +335,9 @@ class Ensemble(_Context):
 
     def __init__(self, replicas, r_c, r_s, skin, p, dt, gamma=0.0, precision=RBL_FP32, full_list=False,
                  subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0, stream=None,
-                 device=None):
+                 device=None, rho_cap=0.0):
         prms = [make_params(rp.L, r_c, r_s, skin, p, dt, rp.T, gamma, rp.seed, precision, full_list,
-                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil) for rp in replicas]
+                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil, rho_cap) for rp in replicas]
         self._create(prms, [len(rp.x) for rp in replicas], stream, device)
         self.offsets = np.concatenate([[0], np.cumsum(self.Ns)])
         x = np.concatenate([rp.x for rp in replicas])
@@ -346,3 +358,8 @@ class Ensemble(_Context):
         if hist is None:
             hist = np.zeros((self.R, nbins), np.int64)
         return self._rdf(dr, nbins, hist)
+
+    def density_profile(self, axis, nbins, hist=None):
+        if hist is None:
+            hist = np.zeros((self.R, nbins), np.int64)
+        return self._profile(axis, nbins, hist)

@@ -167,3 +167,10 @@ def test_rdf_counts_exact(case):
         s = _system(c, x, v, L, full_list=full)
         h = s.rdf(dr, nb)
         assert np.array_equal(h, oracle.rdf_counts(x, L, dr, nb))
+
+
+def test_density_profile_exact(case):
+    c, x, v, L, lists = case
+    s = _system(c, x, v, L)
+    for axis, nb in ((0, 13), (2, 50)):
+        assert np.array_equal(s.density_profile(axis, nb), oracle.density_profile(x, L, axis, nb))

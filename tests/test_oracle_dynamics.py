@@ -124,3 +124,28 @@ def test_rdf_counts_on_fcc():
     for r, z in shells.items():
         assert h[int(r / dr)] == 500 * z, (r, z)
     assert h.sum() == 500 * sum(shells.values())
+
+
+def test_density_profile_counts():
+    """Profile counts: all particles counted; bins agree with floor(x nbins / L)
+    away from bin edges; a liquid-vapour slab shows its two densities."""
+    x, L = inputs.fcc(3000, 0.8, 0.3, seed=4)
+    for axis, nb in ((0, 7), (2, 40)):
+        h = oracle.density_profile(x, L, axis, nb)
+        assert h.sum() == len(x)
+        t = x[:, axis] / L[axis] * nb
+        safe = np.abs(t - np.round(t)) > 1e-6
+        ref = np.bincount(np.floor(t[safe]).astype(int), minlength=nb)
+        h_safe = oracle.density_profile(x[safe], L, axis, nb)
+        assert np.array_equal(h_safe, ref)
+    V = 30.0 * 30.0 * 120.0
+    N = int(round(0.75 * 0.4 * V + 0.01 * 0.6 * V))  # liquid over 40% of z, vapour elsewhere
+    x, L = inputs.slab(N, 30.0, 120.0, 0.75, 0.01, seed=3)
+    nb = 240  # 0.5 sigma bins (single bins alias with the start's lattice planes: average regions)
+    h = oracle.density_profile(x, L, 2, nb)
+    rho = h / (L[0] * L[1] * (L[2] / nb))
+    z = (np.arange(nb) + 0.5) * L[2] / nb
+    liquid = np.abs(z - L[2] / 2) < 0.15 * L[2]
+    vapour = np.abs(z - L[2] / 2) > 0.3 * L[2]
+    assert abs(rho[liquid].mean() - 0.75) < 0.02
+    assert rho[vapour].mean() < 0.05
