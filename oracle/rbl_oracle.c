@@ -207,7 +207,8 @@ void orc_gaussians(uint64_t seed, uint64_t step, uint32_t tag, double out[3])
 /* ------------------------------------------------------------------------- */
 /* Pair classification.  The paper decides core (r < r_c) / shell (r_c <= r < r_s)
  * membership on r_ij (Sec. 2, Eqs. (3)-(4)).  The decision is taken on a 32-bit
- * fixed-point image of each coordinate, u = rint(x * 2^32 / L) mod 2^32, whose
+ * fixed-point image of each coordinate, u = rint(x * 2^32 / L) mod 2^32 (the exact
+ * product rounded once to the nearest integer), whose
  * two's-complement difference is the minimum-image separation in units of
  * L / 2^32; the squared distance is then formed in binary32 with one rounding
  * per operation: d = (float)(int32)(u_i - u_j) * h, r2 = (dx*dx + dy*dy) + dz*dz. */
@@ -227,9 +228,12 @@ static void frame_init(fixed_frame *f, const double L[3])
     }
 }
 
+/* rint(x * 2^32/L) with one rounding: the exact product is rounded to the nearest
+ * integer (ties to even) by a fused multiply-add onto 1.5 * 2^52, whose ulp is 1. */
 static uint32_t quantize1(double x, double inv)
 {
-    return (uint32_t)(uint64_t)llrint(x * inv);
+    const double magic = 6755399441055744.0;
+    return (uint32_t)(uint64_t)(int64_t)(fma(x, inv, magic) - magic);
 }
 
 void orc_quantize(int n, const double *x, const double L[3], uint32_t *u)

@@ -428,13 +428,23 @@ __global__ void __launch_bounds__(kBlock) k_force_finish(View v, int bthreads, i
         for (int a = 0; a < 3; ++a) {
             double m;
             if (fp32) {
-                long long qs = (long long)rsc.fsum_q[a];
-                m = (double)qs * kFixedInv / (double)b.N;
+                // the net force Q, exact in fixed point, is removed exactly: Q = N m + rem
+                // with 0 <= rem < N, and the rem particles of lowest tag take one unit
+                // more, so the corrected forces sum to zero (momentum is conserved)
+                const long long Q = subtract ? (long long)rsc.fsum_q[a] : 0ll;
+                long long mq = Q / b.N, rq = Q - mq * b.N;
+                if (rq < 0) {
+                    mq -= 1;
+                    rq += b.N;
+                }
+                rsc.fcor_q[a] = mq;
+                rsc.fcor_r[a] = rq;
+                m = (double)Q * kFixedInv / (double)b.N;
                 rsc.fsum_q[a] = 0ull;
             } else {
-                m = tot[a] / (double)b.N;
+                m = subtract ? tot[a] / (double)b.N : 0.0;
             }
-            rsc.fcor[a] = subtract ? m : 0.0;
+            rsc.fcor[a] = m;
         }
         if (energy) {
             rsc.energy = tot[3];
@@ -453,12 +463,17 @@ __global__ void k_store_forces(View v, double *out)
     const int r = slot_replica(v, i, live);
     if (!live) return;
     size_t N = (size_t)v.N;
-    size_t t = (size_t)v.box[r].in0 + (size_t)v.tag[i];
+    const int tag = v.tag[i];
+    size_t t = (size_t)v.box[r].in0 + (size_t)tag;
+    const RepScalars &rsc = v.rs[r];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double f = v.precision == RBL_FP32 ? (double)((const long long *)v.F)[a * N + i] * kFixedInv
-                                           : ((const double *)v.F)[a * N + i];
-        out[t * 3 + a] = f - v.rs[r].fcor[a];
+        if (v.precision == RBL_FP32) {
+            const long long q = ((const long long *)v.F)[a * N + i] - rsc.fcor_q[a] - (tag < rsc.fcor_r[a] ? 1 : 0);
+            out[t * 3 + a] = (double)q * kFixedInv;
+        } else {
+            out[t * 3 + a] = ((const double *)v.F)[a * N + i] - rsc.fcor[a];
+        }
     }
 }
 

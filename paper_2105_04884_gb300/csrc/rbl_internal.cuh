@@ -39,6 +39,8 @@ struct DevScalars {
 struct RepScalars {
     unsigned long long fsum_q[3];   // FP32 path: sum of fixed-point forces (mod 2^64)
     double fcor[3];                 // mean force subtracted from every particle
+    long long fcor_q[3];            // FP32 path: the net force Q (fixed point) as Q = N fcor_q + fcor_r,
+    long long fcor_r[3];            // 0 <= fcor_r < N; tags < fcor_r subtract fcor_q + 1, the rest fcor_q
     double energy, virial;          // RBL estimates from the last evaluation
     double u_exact, w_exact;        // unsampled energy and virial (on demand)
     double ksum;                    // sum v^2 (on demand)
@@ -464,12 +466,12 @@ __device__ __forceinline__ double f32_to_double(float f)
     return __longlong_as_double((long long)r);
 }
 
-// Fixed-point image of a coordinate x in [0, L): rint(x * 2^32/L) mod 2^32, the
-// product and the rounding taken as two separate FP64 operations.
+// Fixed-point image of a coordinate x in [0, L): rint(x * 2^32/L) mod 2^32 with a
+// single rounding: one fused multiply-add onto 1.5 * 2^52, whose ulp is 1, rounds
+// the exact product to the nearest integer (ties to even).
 __device__ __forceinline__ unsigned quantize(double x, double inv)
 {
-    double t = __dmul_rn(x, inv);
-    double y = __dadd_rn(t, 6755399441055744.0); // 1.5 * 2^52: rounds to an integer
+    const double y = __fma_rn(x, inv, 6755399441055744.0);
     return (unsigned)(unsigned long long)__double_as_longlong(y);
 }
 

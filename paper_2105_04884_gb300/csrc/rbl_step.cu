@@ -74,21 +74,14 @@ __global__ void k_store(View v, double *x, double *vel)
     }
 }
 
-template <bool FP32>
-__device__ __forceinline__ double force_component(const View &v, int a, int i, double fcor)
-{
-    size_t N = (size_t)v.N;
-    if (FP32) {
-        long long q = ((const long long *)v.F)[a * N + i];
-        return fma(i64_to_double(q), kFixedInv, -fcor);
-    } else {
-        return ((const double *)v.F)[a * N + i] - fcor;
-    }
-}
-
-// ck: kick coefficient (dt/2 or dt).  DRIFT = false: kick only (closing half-kick).
+// ck: kick coefficient (dt/2 or dt); cks = ck 2^-24, the kick per fixed-point unit
+// of force.  DRIFT = false: kick only (closing half-kick).
+//
+// FP32 path: the corrected force of particle i is the integer q_i - m - [tag < r]
+// (the net force removed exactly, see k_force_finish), converted exactly and
+// applied with one fused multiply-add: v += cks (q_i - m - [tag < r]).
 template <bool FP32, bool LANGEVIN, bool DRIFT>
-__global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
+__global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck, double cks)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= v.N) return;
@@ -98,11 +91,16 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
     const Box &b = v.box[r];
     size_t N = (size_t)v.N;
     const RepScalars *rsc = v.rs + r;
+    const int tag = v.tag[i];
     double vv[3], xx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double f = force_component<FP32>(v, a, i, rsc->fcor[a]);
-        vv[a] = fma(ck, f, v.v[a * N + i]);
+        if (FP32) {
+            const long long q = ((const long long *)v.F)[a * N + i] - rsc->fcor_q[a] - (tag < rsc->fcor_r[a] ? 1 : 0);
+            vv[a] = fma(cks, i64_to_double(q), v.v[a * N + i]);
+        } else {
+            vv[a] = fma(ck, ((const double *)v.F)[a * N + i] - rsc->fcor[a], v.v[a * N + i]);
+        }
     }
     if constexpr (!DRIFT) {
 #pragma unroll
@@ -110,7 +108,6 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck)
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) xx[a] = v.x[a * N + i];
-        int tag = v.tag[i];
         if (LANGEVIN) {
             const double half = 0.5 * v.dt;
 #pragma unroll
@@ -288,15 +285,16 @@ cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t 
     int g = ceil_div(v.N, kBlock);
     bool fp32 = v.precision == RBL_FP32;
     bool lang = v.gamma > 0.0;
+    const double cks = ck * kFixedInv;
     if (!drift) {
-        if (fp32) k_integrate<true, false, false><<<g, kBlock, 0, s>>>(v, ck);
-        else k_integrate<false, false, false><<<g, kBlock, 0, s>>>(v, ck);
+        if (fp32) k_integrate<true, false, false><<<g, kBlock, 0, s>>>(v, ck, cks);
+        else k_integrate<false, false, false><<<g, kBlock, 0, s>>>(v, ck, cks);
     } else if (fp32) {
-        if (lang) k_integrate<true, true, true><<<g, kBlock, 0, s>>>(v, ck);
-        else k_integrate<true, false, true><<<g, kBlock, 0, s>>>(v, ck);
+        if (lang) k_integrate<true, true, true><<<g, kBlock, 0, s>>>(v, ck, cks);
+        else k_integrate<true, false, true><<<g, kBlock, 0, s>>>(v, ck, cks);
     } else {
-        if (lang) k_integrate<false, true, true><<<g, kBlock, 0, s>>>(v, ck);
-        else k_integrate<false, false, true><<<g, kBlock, 0, s>>>(v, ck);
+        if (lang) k_integrate<false, true, true><<<g, kBlock, 0, s>>>(v, ck, cks);
+        else k_integrate<false, false, true><<<g, kBlock, 0, s>>>(v, ck, cks);
     }
     return cudaGetLastError();
 }

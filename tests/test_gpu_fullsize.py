@@ -5,8 +5,8 @@ Langevin gamma = 1, dt = 0.005, K = 2 -- the launch configuration bench.py times
 After 20 steps on the graph path, sampled particles are checked one by one against
 the oracle (which tests every other particle for each of them): core and shell
 rows and batches bit-exact, un-subtracted forces within the FP32 bar.  Properties
-that hold at any size are checked on every particle: the mean-subtracted force
-sums to zero and differs from the raw force by one constant vector."""
+that hold at any size are checked on every particle: the corrected force sums to
+exactly zero and differs from the raw force by the fixed-point mean."""
 import numpy as np
 import pytest
 
@@ -63,11 +63,14 @@ def test_sampled_rows_batches_forces(run):
 
 
 def test_net_force_properties(run):
+    """The net force is removed exactly in fixed point (units of 2^-24): the corrected
+    forces sum to zero exactly, and each differs from the raw force by the mean
+    rounded down or up to the fixed-point grid (the remainder spread over the
+    particles of lowest tag)."""
     F_sub, F_raw = run["F_sub"], run["F_raw"]
-    rms = np.sqrt(np.mean(np.sum(F_raw ** 2, axis=1)))
-    # the subtracted force has zero sum (up to the int64 -> double rounding)
-    assert np.all(np.abs(F_sub.sum(axis=0)) <= 1e-6 * rms * N ** 0.5)
-    # and differs from the raw force by one vector, the raw mean
+    unit = 2.0 ** -24
+    assert np.all(F_sub.sum(axis=0) == 0.0)
     d = F_raw - F_sub
-    assert np.all(np.abs(d - d[0]) <= 1e-9 * rms)
-    assert np.allclose(d[0], F_raw.mean(axis=0), rtol=0, atol=1e-9 * rms)
+    lo = np.floor(F_raw.sum(axis=0) / unit / N) * unit
+    assert np.all((d == lo) | (d == lo + unit))
+    assert np.all(np.abs(d.mean(axis=0) - F_raw.mean(axis=0)) <= 1e-12)
