@@ -212,6 +212,17 @@ rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
  * cleared).  Synchronises. */
 rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *hist);
 
+/* Launch shapes, which no result depends on (the tests check this bit for bit):
+ * threads per block of the force kernel (64, 128 or 256; default 128) and home
+ * cells (warps) per block of the list build (2, 4 or 8; default 4).
+ * rbl_autotune times every candidate of each on the current state (`trials`
+ * launches each, after one warm-up) and keeps the fastest, reporting the choice
+ * through the optional out pointers.  It times the list build on the images of the
+ * last build, so the lists, the particle order, the state, the step counter and the
+ * per-replica counters are as they were afterwards.  Synchronises. */
+rbl_status rbl_set_launch_config(rbl_ctx *ctx, int force_threads, int build_warps);
+rbl_status rbl_autotune(rbl_ctx *ctx, int trials, int *force_threads, int *build_warps);
+
 /* Phase timing.  While enabled, rbl_step launches each step's phases directly (no
  * graph replay) and brackets them with CUDA events on the context's stream:
  * phase 0 = kick/drift/thermostat kernel, 1 = rebuild chain (device-conditional:

@@ -271,17 +271,17 @@ __global__ void k_copy_back(View v, int conditional)
 // Candidates are visited in canonical order, so list order and bit order are the
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
 // k.  Row lengths are counted past the core capacity.
-constexpr int kBuildWarps = 4;
+constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
-__global__ void __launch_bounds__(kBuildWarps * 32) k_build_lists(View v, int conditional)
+__global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int conditional)
 {
     if (skip(v, conditional)) return;
-    __shared__ int s_pre[kBuildWarps][kMaxSeg + 1];
-    __shared__ int s_a[kBuildWarps][kMaxSeg], s_la[kBuildWarps][kMaxSeg], s_b[kBuildWarps][kMaxSeg];
-    __shared__ int4 s_pos[kBuildWarps][32];
-    __shared__ int s_j[kBuildWarps][32];
+    __shared__ int s_pre[kMaxBuildWarps][kMaxSeg + 1];
+    __shared__ int s_a[kMaxBuildWarps][kMaxSeg], s_la[kMaxBuildWarps][kMaxSeg], s_b[kMaxBuildWarps][kMaxSeg];
+    __shared__ int4 s_pos[kMaxBuildWarps][32];
+    __shared__ int s_j[kMaxBuildWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kBuildWarps + warp;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= v.ncell) return; // whole warp; no block-wide barrier below
     const int r = v.cell_rep[c];
     const Box &b = v.box[r];
@@ -465,7 +465,7 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_sort_cells<<<gC, kBlock, 0, s>>>(v, cond);
     k_permute<<<gN, kBlock, 0, s>>>(v, cond);
     k_copy_back<<<gN, kBlock, 0, s>>>(v, cond);
-    k_build_lists<<<ceil_div(v.ncell, kBuildWarps), kBuildWarps * 32, 0, s>>>(v, cond);
+    k_build_lists<<<ceil_div(v.ncell, v.build_warps), v.build_warps * 32, 0, s>>>(v, cond);
     k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
     k_finish_all<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();

@@ -237,6 +237,8 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.full_list = prm->full_list ? 1 : 0;
     v.precision = prm->precision;
     v.subtract = prm->subtract_net_force ? 1 : 0;
+    v.force_threads = 128;
+    v.build_warps = 4;
     v.ncell = P.ncell;
     const double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;
     const double lo = rc - sk > 0.0 ? rc - sk : 0.0;
@@ -918,6 +920,100 @@ rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *his
     if (st != RBL_OK) return st;
     for (size_t b = 0; b < nh; ++b) hist[b] += (long long)h[b];
     return RBL_OK;
+}
+
+rbl_status rbl_set_launch_config(rbl_ctx *ctx, int force_threads, int build_warps)
+{
+    if (!ctx) return RBL_EINVAL;
+    if (force_threads != 64 && force_threads != 128 && force_threads != 256) {
+        set_err(ctx, "force_threads must be 64, 128 or 256 (got %d)", force_threads);
+        return RBL_EINVAL;
+    }
+    if (build_warps != 2 && build_warps != 4 && build_warps != 8) {
+        set_err(ctx, "build_warps must be 2, 4 or 8 (got %d)", build_warps);
+        return RBL_EINVAL;
+    }
+    if (ctx->view.force_threads != force_threads || ctx->view.build_warps != build_warps) {
+        ctx->view.force_threads = force_threads;
+        ctx->view.build_warps = build_warps;
+        if (ctx->graph_exec) { // the captured step holds the old launch shapes
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+        }
+    }
+    return RBL_OK;
+}
+
+rbl_status rbl_autotune(rbl_ctx *ctx, int trials, int *force_threads, int *build_warps)
+{
+    if (!ctx || trials < 1) return RBL_EINVAL;
+    rbl_status st = ensure_lists(ctx);
+    if (st != RBL_OK) return st;
+    // the trials rebuild and re-evaluate: keep the per-replica scalars (rebuild
+    // counts, build statistics, energies) as they were
+    st = read_scalars(ctx, true);
+    if (st != RBL_OK) return st;
+    std::vector<RepScalars> saved(ctx->h_rs, ctx->h_rs + ctx->R);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int ft[3] = {64, 128, 256}, bw[3] = {2, 4, 8};
+    float best_f = 1e30f, best_b = 1e30f;
+    int pick_f = ctx->view.force_threads, pick_b = ctx->view.build_warps;
+    cudaError_t e = cudaSuccess;
+    // List build, timed on the images of the last build (ubuild) in place of the
+    // current ones: the particles are already in that build's cell order, so the
+    // permutation is the identity and the lists come out as they were; the current
+    // images and the trajectory are untouched.
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        View v = ctx->view;
+        v.build_warps = bw[k];
+        v.pos = v.ubuild;
+        e = launch_rebuild(v, ctx->n_scan_blocks, false, ctx->stream); // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t)
+            e = launch_rebuild(v, ctx->n_scan_blocks, false, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_b) {
+            best_b = ms;
+            pick_b = bw[k];
+        }
+    }
+    // force kernel and its reduction (the step counter is not advanced)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        View v = ctx->view;
+        v.force_threads = ft[k];
+        e = launch_forces(v, 0, 0, false, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) e = launch_forces(v, 0, 0, false, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_f) {
+            best_f = ms;
+            pick_f = ft[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        set_err(ctx, "autotune failed: %s", cudaGetErrorString(e));
+        return RBL_ECUDA;
+    }
+    CK(cudaMemcpyAsync(ctx->view.rs, saved.data(), sizeof(RepScalars) * (size_t)ctx->R, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->force_valid = 0;
+    ctx->energy_valid = 0;
+    st = rbl_set_launch_config(ctx, pick_f, pick_b);
+    if (st != RBL_OK) return st;
+    if (force_threads) *force_threads = pick_f;
+    if (build_warps) *build_warps = pick_b;
+    return check_flags(ctx);
 }
 
 rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable)

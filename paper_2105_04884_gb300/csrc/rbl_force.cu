@@ -28,22 +28,26 @@ __device__ __forceinline__ T warp_sum(T x)
     return x;
 }
 
-// Deterministic block sum (fixed tree) of NV doubles per thread into out[0..NV).
-template <int NV, int BLOCK>
-__device__ __forceinline__ void block_sum_d(double (&x)[NV], double *out)
+// Deterministic partial sums of NV doubles per thread, one partial per 64-thread
+// group whatever the block size (64, 128 or 256): warp sums by a fixed shuffle
+// tree, then the group's two warps in order, into partials[group][off..off+NV).
+// The reductions built on them therefore do not depend on the launch shape.
+constexpr int kMaxForceThreads = 256;
+template <int NV>
+__device__ __forceinline__ void group_sums(double (&x)[NV], double *partials, int off)
 {
-    __shared__ double sh[NV][BLOCK / 32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double sh[NV][kMaxForceThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, ng = blockDim.x >> 6;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double s = warp_sum(x[k]);
         if (lane == 0) sh[k][wid] = s;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < BLOCK / 32; ++w) s += sh[threadIdx.x][w];
-        out[threadIdx.x] = s;
+    if ((int)threadIdx.x < NV * ng) {
+        const int g = threadIdx.x / NV, k = threadIdx.x - g * NV;
+        const size_t group = (size_t)blockIdx.x * ng + g;
+        partials[group * 8 + off + k] = sh[k][2 * g] + sh[k][2 * g + 1];
     }
 }
 
@@ -156,19 +160,29 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 // across the warp), the batch is drawn while those loads are in flight, and
 // neighbour indices and positions are gathered kGather at a time before their pair
 // terms are computed.
-constexpr int kForceThreads = 128;
-static_assert(kForceThreads >= kMinBlock, "per-block partials are sized for kMinBlock");
+// Threads per block: a launch parameter of the context (64, 128 or 256; chosen by
+// rbl_autotune); the staging arrays are dynamic shared memory sized for the block.
+// FP32 registers are capped so that 7 blocks of 128 threads fit an SM (the FP64
+// path needs more and runs at the FP64 rate anyway).
+#ifndef RBL_FORCE_REGS
+#define RBL_FORCE_REGS 72
+#endif
+constexpr int kForceRegs = RBL_FORCE_REGS;
+static_assert(kMinBlock == 64 && kMaxForceThreads % 64 == 0, "per-block partials are sized for kMinBlock");
 constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
 constexpr int kGather = 8;
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX>
-__global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset)
+__global__ void __maxnreg__(FP32 ? kForceRegs : 128) k_force(View v, int step_offset)
 {
-    __shared__ unsigned s_mask[kMaskStage][kForceThreads];
-    __shared__ unsigned short s_pref[kMaskStage][kForceThreads]; // set bits before each staged word
+    // staged mask words [kMaskStage][blockDim] and the set bits before each of them
+    extern __shared__ unsigned s_dyn[];
+    const int bd = blockDim.x;
+    unsigned *s_mask = s_dyn;
+    unsigned short *s_pref = (unsigned short *)(s_dyn + kMaskStage * bd);
     const unsigned long long step = v.sc->step + (unsigned long long)step_offset;
     const int t = threadIdx.x;
-    const int i = blockIdx.x * kForceThreads + t;
+    const int i = blockIdx.x * bd + t;
     const size_t N = (size_t)v.N;
     long long qv[3] = {0, 0, 0};
     double f64[3] = {0.0, 0.0, 0.0};
@@ -193,13 +207,13 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (w0 + u < nws) {
-                    s_mask[w0 + u][t] = tmp[u];
-                    s_pref[w0 + u][t] = (unsigned short)run;
+                    s_mask[(w0 + u) * bd + t] = tmp[u];
+                    s_pref[(w0 + u) * bd + t] = (unsigned short)run;
                     run += __popc(tmp[u]);
                 }
         }
         auto mask_word = [&](int w) -> unsigned {
-            return w < kMaskStage ? s_mask[w][t] : v.mask[(size_t)w * N + i];
+            return w < kMaskStage ? s_mask[w * bd + t] : v.mask[(size_t)w * N + i];
         };
         Accum<FP32, ENERGY> acc;
         acc.zero(b);
@@ -234,10 +248,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
 #pragma unroll
                         for (int sw = kMaskStage / 2; sw >= 1; sw >>= 1) {
                             const int mid = w + sw;
-                            const int pm = (int)s_pref[min(mid, kMaskStage - 1)][t];
+                            const int pm = (int)s_pref[min(mid, kMaskStage - 1) * bd + t];
                             w = (mid < nws && pm <= tq) ? mid : w;
                         }
-                        const int cand = (w << 5) + select_bit(s_mask[w][t], tq - (int)s_pref[w][t]);
+                        const int cand = (w << 5) + select_bit(s_mask[w * bd + t], tq - (int)s_pref[w * bd + t]);
                         int sg = 0;
 #pragma unroll
                         for (int sw = 32; sw >= 1; sw >>= 1) {
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
     // Total force and energy/virial partials.
     if (MODE == 2) {
         double x[2] = {e_i, w_i};
-        block_sum_d<2, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8 + 3);
+        group_sums<2>(x, v.partials, 3);
     } else if (FP32) {
         int lane = threadIdx.x & 31;
 #pragma unroll
@@ -385,17 +399,17 @@ __global__ void __launch_bounds__(kForceThreads) k_force(View v, int step_offset
         }
         if (ENERGY) {
             double x[2] = {e_i, w_i};
-            block_sum_d<2, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8 + 3);
+            group_sums<2>(x, v.partials, 3);
         }
     } else {
         double x[5] = {f64[0], f64[1], f64[2], e_i, w_i};
-        block_sum_d<5, kForceThreads>(x, v.partials + (size_t)blockIdx.x * 8);
+        group_sums<5>(x, v.partials, 0);
     }
 }
 
-// One block per replica: reduce its blocks' partials in a fixed order, form its
-// mean force F_cor (Appendix A) and reset its integer accumulator for the next
-// evaluation.  bthreads: threads of the blocks that wrote the partials.
+// One block per replica: reduce its 64-thread groups' partials in a fixed order,
+// form its mean force F_cor (Appendix A) and reset its integer accumulator for the
+// next evaluation.  bthreads: threads per partial (64).
 // exact = 1: store the unsampled energy and virial only (MODE 2 partials).
 __global__ void __launch_bounds__(kBlock) k_force_finish(View v, int bthreads, int fp32, int energy, int subtract,
                                                          int advance, int exact)
@@ -552,29 +566,49 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
 
 } // namespace
 
+// Launch k_force with the context's block size and its staging in dynamic shared
+// memory (opting in to more than the default 48 KB where the largest block needs it).
+template <int MODE, bool FP32, bool ENERGY, int PMAX>
+cudaError_t launch_k_force(const View &v, int step_offset, cudaStream_t s)
+{
+    const int bd = v.force_threads;
+    const size_t smem = (size_t)kMaskStage * bd * (sizeof(unsigned) + sizeof(unsigned short));
+    if (smem > 40 * 1024) {
+        // beyond the default limit together with the kernel's static shared memory:
+        // a function attribute, set outside stream capture (a step always launches
+        // this kernel directly before its graph is captured)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+            e = cudaFuncSetAttribute(k_force<MODE, FP32, ENERGY, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_force<MODE, FP32, ENERGY, PMAX><<<ceil_div(v.N, bd), bd, smem, s>>>(v, step_offset);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool FP32, bool ENERGY>
 cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kForceThreads);
     if constexpr (MODE == 1) {
-        k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
+        return launch_k_force<MODE, FP32, ENERGY, 0>(v, step_offset, s);
     } else {
         // every rank slot up to PMAX is resolved, so PMAX is p itself for the usual
         // batch sizes and a bound otherwise
         switch (v.p) {
-        case 1: k_force<MODE, FP32, ENERGY, 1><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
-        case 2: k_force<MODE, FP32, ENERGY, 2><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
-        case 5: k_force<MODE, FP32, ENERGY, 5><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
-        case 10: k_force<MODE, FP32, ENERGY, 10><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
-        case 20: k_force<MODE, FP32, ENERGY, 20><<<g, kForceThreads, 0, s>>>(v, step_offset); break;
+        case 1: return launch_k_force<MODE, FP32, ENERGY, 1>(v, step_offset, s);
+        case 2: return launch_k_force<MODE, FP32, ENERGY, 2>(v, step_offset, s);
+        case 5: return launch_k_force<MODE, FP32, ENERGY, 5>(v, step_offset, s);
+        case 10: return launch_k_force<MODE, FP32, ENERGY, 10>(v, step_offset, s);
+        case 20: return launch_k_force<MODE, FP32, ENERGY, 20>(v, step_offset, s);
         default:
-            if (v.p <= 8) k_force<MODE, FP32, ENERGY, 8><<<g, kForceThreads, 0, s>>>(v, step_offset);
-            else if (v.p <= 16) k_force<MODE, FP32, ENERGY, 16><<<g, kForceThreads, 0, s>>>(v, step_offset);
-            else if (v.p <= 32) k_force<MODE, FP32, ENERGY, 32><<<g, kForceThreads, 0, s>>>(v, step_offset);
-            else k_force<MODE, FP32, ENERGY, 0><<<g, kForceThreads, 0, s>>>(v, step_offset);
+            if (v.p <= 8) return launch_k_force<MODE, FP32, ENERGY, 8>(v, step_offset, s);
+            if (v.p <= 16) return launch_k_force<MODE, FP32, ENERGY, 16>(v, step_offset, s);
+            if (v.p <= 32) return launch_k_force<MODE, FP32, ENERGY, 32>(v, step_offset, s);
+            return launch_k_force<MODE, FP32, ENERGY, 0>(v, step_offset, s);
         }
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s)
@@ -592,19 +626,18 @@ cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStr
 {
     bool fp32 = v.precision == RBL_FP32;
     int threads = (fp32 && !energy) ? 32 : kBlock;
-    k_force_finish<<<v.R, threads, 0, s>>>(v, kForceThreads, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract,
+    k_force_finish<<<v.R, threads, 0, s>>>(v, kMinBlock, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract,
                                            advance, 0);
     return cudaGetLastError();
 }
 
-int force_block_threads() { return kForceThreads; }
 
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kForceThreads);
-    if (v.precision == RBL_FP32) k_force<2, true, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
-    else k_force<2, false, true, 0><<<g, kForceThreads, 0, s>>>(v, 0);
-    k_force_finish<<<v.R, kBlock, 0, s>>>(v, kForceThreads, 0, 1, 0, 0, 1);
+    cudaError_t e = v.precision == RBL_FP32 ? launch_k_force<2, true, true, 0>(v, 0, s)
+                                            : launch_k_force<2, false, true, 0>(v, 0, s);
+    if (e != cudaSuccess) return e;
+    k_force_finish<<<v.R, kBlock, 0, s>>>(v, kMinBlock, 0, 1, 0, 0, 1);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,8 @@ struct View {
     int R;                          // replicas
     int ntile;                      // N / kTile
     int p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
+    int force_threads;              // threads per block of the force kernel (64, 128 or 256)
+    int build_warps;                // home cells (warps) per block of the list build (2, 4 or 8)
     int ncell;                      // cells of all replicas, pad cells included
     float t_core_list, t_shell_lo, t_cut_list, t_rc2, t_rs2, t_disp;
     double dt, gamma, c1;
@@ -544,5 +546,4 @@ cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);
 constexpr int kMaxProfileBins = 12288; // shared-memory histogram of one block
-int force_block_threads();
 } // namespace rbl

@@ -56,7 +56,8 @@ class rbl_obs(ctypes.Structure):
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
            "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state", "rbl_build_lists",
            "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
-           "rbl_get_batch", "rbl_rdf", "rbl_density_profile", "rbl_set_phase_timing", "rbl_phase_times",
+           "rbl_get_batch", "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config",
+           "rbl_autotune", "rbl_set_phase_timing", "rbl_phase_times",
            "rbl_forces_static", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
 
 _lib = None
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = False):
     L.rbl_get_batch.argtypes = [P, LL, P, P]
     L.rbl_rdf.argtypes = [P, ctypes.c_float, I, P]
     L.rbl_density_profile.argtypes = [P, I, I, P]
+    L.rbl_set_launch_config.argtypes = [P, I, I]
+    L.rbl_autotune.argtypes = [P, I, P, P]
     L.rbl_set_phase_timing.argtypes = [P, I]
     L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
     L.rbl_forces_static.argtypes = [ctypes.POINTER(rbl_params), I, P, LL, P, P]
@@ -268,6 +271,16 @@ class _Context:
         counts = np.zeros(self.N, np.int32)
         self._check(self.lib.rbl_get_batch(self.h, int(step), _ptr(batch), _ptr(counts)))
         return batch, counts
+
+    def set_launch_config(self, force_threads=128, build_warps=4):
+        self._check(self.lib.rbl_set_launch_config(self.h, int(force_threads), int(build_warps)))
+
+    def autotune(self, trials=5):
+        """Pick the fastest launch shapes on the current state; returns them."""
+        ft = ctypes.c_int()
+        bw = ctypes.c_int()
+        self._check(self.lib.rbl_autotune(self.h, int(trials), ctypes.byref(ft), ctypes.byref(bw)))
+        return {"force_threads": ft.value, "build_warps": bw.value}
 
     def set_phase_timing(self, enable=True):
         self._check(self.lib.rbl_set_phase_timing(self.h, int(bool(enable))))
