@@ -262,6 +262,7 @@ def ensemble_bench(a, rank, timed):
     ntot = sum(rp.N for rp in reps)
     ens = rbl.Ensemble(reps, **shared)
     ens.step(a.warmup)
+    ens_cfg = ens.autotune(trials=3)
     K = a.ensemble_steps
     ms, _ = timed(ens, K, phases=False)
     obs = ens.observables()
@@ -283,6 +284,7 @@ def ensemble_bench(a, rank, timed):
     return {"workload": "lj_ensemble_R256_N500-20000_rho0.6-0.9_T1-2_rc1.5_rs3.5_p10_nvt", "replicas": e["R"],
             "particles": ntot, "steps": K, "value": ntot * K / (ms * 1e-3), "unit": "particle-steps/s",
             "ms_per_step": ms / K, "rebuilds_per_replica_mean": sum(o["n_rebuild"] for o in obs) / e["R"],
+            "launch_config": ens_cfg,
             "separate_contexts": {"value": ntot * k / t_single, "steps": k,
                                   "ms_per_step": t_single * 1e3 / k}}
 
@@ -315,6 +317,8 @@ def slab_bench(a, rank, timed):
     prof = {}
     for name, full in (("rbl", False), ("full_list", True)):
         s = rbl.System(x, v, L, full_list=full, **common)
+        s.step(3)
+        s.autotune(trials=2)
         ms, _ = timed(s, c["steps"], phases=False)
         h = np.zeros(nb, np.int64)
         for _ in range(5):
@@ -436,7 +440,9 @@ def run_ours(a, rank, world, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        torch.cuda.nvtx.range_push("timed")  # profilers can restrict captures to this range
         system.step(K)
+        torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -447,6 +453,7 @@ def run_ours(a, rank, world, local):
                   seed=1 + rank, cells_per_cutoff=w["K"], precision=rbl.RBL_FP32)
     s = rbl.System(x, v, L, **common)
     s.step(a.warmup)
+    tuned = s.autotune(trials=3)  # launch shapes only: no result depends on them
     obs0 = s.observables()
     clocks = Clocks(local)
     clocks.start()
@@ -481,7 +488,9 @@ def run_ours(a, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set > L2 (lists %.0f MB)" % (4 * N * (nc + obs["Ns_mean"]) / 1e6),
                    "timed_path": "direct launches with per-phase CUDA events"},
-        "gpu_launches": 14 * a.steps + 1,
+        # per step: integrate, 12 rebuild-chain kernels (each returns at once when no
+        # rebuild is due), force kernel, force reduction; plus the closing half-kick
+        "gpu_launches": 15 * a.steps + 1,
         "phases_ms_per_step": {"integrate": phase_ms[0] / nsteps, "rebuild_chain": phase_ms[1] / nsteps,
                                "force_kernel": phase_ms[2] / nsteps, "force_reduce": phase_ms[3] / nsteps},
         "graph_replay_ms_per_step": ms_graph / a.steps,
@@ -492,6 +501,7 @@ def run_ours(a, rank, world, local):
                      "algorithmic_bytes_per_particle": alg_bytes_pp,
                      "traffic": traffic, "traffic_per": "launch"},
         "clocks": clk,
+        "launch_config": tuned,
     }
     # full Verlet list on the same GPU and workload
     if not a.no_full_list:
@@ -499,6 +509,7 @@ def run_ours(a, rank, world, local):
         torch.cuda.empty_cache()
         sf = rbl.System(x, v, L, full_list=True, **common)
         sf.step(a.warmup)
+        sf.autotune(trials=3)
         msf, (pmf, nf) = timed(sf, a.steps, phases=True)
         vf = N * a.steps * world / (msf * 1e-3)
         of = sf.observables()
@@ -511,6 +522,7 @@ def run_ours(a, rank, world, local):
         # RBL trajectory match the full list's; see "matched_physics")
         s2 = rbl.System(x, v, L, **dict(common, r_c=2.0))
         s2.step(a.warmup)
+        s2.autotune(trials=3)
         ms2, (pm2, n2) = timed(s2, a.steps, phases=True)
         v2 = N * a.steps * world / (ms2 * 1e-3)
         result["rbl_rc2.0"] = {"value": v2, "ms_per_step": ms2 / a.steps, "force_kernel_ms": pm2[2] / n2,
@@ -525,6 +537,7 @@ def run_ours(a, rank, world, local):
         se = rbl.System(x, v, L, **common)
         se.set_phase_timing(False)
         se.step(a.warmup)
+        se.autotune(trials=3)
         xh = torch.from_numpy(x).pin_memory()
         vh = torch.from_numpy(v).pin_memory()
         xo = torch.empty_like(xh).pin_memory()
