@@ -79,6 +79,8 @@ def _declare(L):
     L.orc_lj.argtypes = [I, P, P, P]
     L.orc_rbl_forces.argtypes = [I, P, P, D, D, D, I, U64, U64, P, P, I, P, P, I, P, P, P, P]
     L.orc_rbl_forces.restype = I
+    L.orc_build_pool.argtypes = [I, P, P, D, D, D, I, I, P, P, P, P, P]
+    L.orc_build_pool.restype = I
     L.orc_sample.argtypes = [I, P, P, D, D, D, I, I, U64, U64, I, P, I, I, P, P, P, P, P, P, P]
     L.orc_sample.restype = I
     L.orc_full_forces.argtypes = [I, P, P, D, P, P, I, P, P]
@@ -229,6 +231,26 @@ def rbl_forces(x, L, rc, rs, skin, p, seed, step, lists, want_batch=False):
                          lists.core.shape[1], _p(lists.shell), _p(lists.n_shell), lists.shell.shape[1], _p(F),
                          _p(ev), _p(batch), _p(bn))
     return F, ev, batch, bn
+
+
+def build_pool(x, L, rc, rs, skin, cap_core=160, cap_pool=6000):
+    """The paper's own sampling (Sec. 2): core rows and the stencil pool of every
+    particle on the grid of edge >= r_c + skin; returned as Lists whose shell rows
+    are the pools, so rbl_forces() evaluates the paper-literal estimator."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    core = np.full((n, cap_core), -1, np.int32)
+    pool = np.full((n, cap_pool), -1, np.int32)
+    nc = np.zeros(n, np.int32)
+    npl = np.zeros(n, np.int32)
+    gn = np.zeros(3, np.int32)
+    st = lib().orc_build_pool(n, _p(x), _p(_f64(L)), rc, rs, skin, cap_core, cap_pool, _p(core), _p(nc), _p(pool),
+                              _p(npl), _p(gn))
+    if st != 0:
+        raise OverflowError("oracle row exceeded its capacity")
+    out = Lists(core, nc, pool, npl)
+    out.grid = gn
+    return out
 
 
 class Sample:

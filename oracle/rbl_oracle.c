@@ -1043,3 +1043,84 @@ void orc_density_profile(int n, const double *x, const double L[3], int axis, in
         hist[(int)(((uint64_t)u * (uint64_t)nbins) >> 32)] += 1;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* The paper's own sampling pool (Sec. 2, Fig. 1).  The box is cut into cells of
+ * edge at least r_c + skin (n_a = floor(L_a / (r_c + skin)); the paper's "slightly
+ * larger than r_c").  The pool I(i) is every particle j != i in the stencil of
+ * (2m + 1)^3 cells centred on i's cell, m = floor(r_s / r_c) + 1 (fewer cells, each
+ * once, on an axis with fewer than 2m + 1), in canonical order (stencil slot, u_x,
+ * tag) on that grid.  The core row, j != i with r2 < (r_c + skin)^2, is sorted the
+ * same way.  A batch is then drawn from the pool exactly as from a shell row and
+ * scaled by N_I / p (Eq. (4) with N_I), so orc_rbl_forces applies unchanged with
+ * the pool in place of the shell rows.  Brute force over all pairs.              */
+/* ------------------------------------------------------------------------- */
+static void grid_init_pool(cell_grid *g, const double L[3], double rc, double rs, double skin)
+{
+    const int m = (int)floor(rs / rc) + 1;
+    for (int a = 0; a < 3; ++a) {
+        int n = (int)floor(L[a] / (rc + skin));
+        if (n < 1) n = 1;
+        g->n[a] = n;
+        if (n >= 2 * m + 1) {
+            g->nofs[a] = 2 * m + 1;
+            for (int o = 0; o < 2 * m + 1; ++o) g->ofs[a][o] = o - m;
+        } else {
+            g->nofs[a] = n;
+            for (int o = 0; o < n; ++o) g->ofs[a][o] = o;
+        }
+    }
+}
+
+int orc_build_pool(int n, const double *x, const double L[3], double rc, double rs, double skin, int cap_core,
+                   int cap_pool, int32_t *core, int32_t *n_core, int32_t *pool, int32_t *n_pool, int32_t *grid_n)
+{
+    fixed_frame f;
+    frame_init(&f, L);
+    thresholds t = make_thresholds(rc, rs, skin);
+    cell_grid g;
+    grid_init_pool(&g, L, rc, rs, skin);
+    if (grid_n)
+        for (int a = 0; a < 3; ++a) grid_n[a] = g.n[a];
+    uint32_t *u = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)n);
+    int *cells3 = (int *)malloc(sizeof(int) * 3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) u[3 * i + a] = quantize1(x[3 * i + a], f.inv[a]);
+        cell_of(&g, u + 3 * i, cells3 + 3 * i);
+    }
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        int maxcap = cap_core > cap_pool ? cap_core : cap_pool;
+        row_key *scratch = (row_key *)malloc(sizeof(row_key) * (size_t)(maxcap + 1));
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            int nc = 0, np = 0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                if (stencil_slot(&g, cells3 + 3 * i, cells3 + 3 * j) >= 0) {
+                    if (np < cap_pool) pool[(size_t)i * cap_pool + np] = j;
+                    ++np;
+                }
+                float r2 = pair_r2f(u + 3 * i, u + 3 * j, f.h);
+                if (r2 < t.core_list) {
+                    if (nc < cap_core) core[(size_t)i * cap_core + nc] = j;
+                    ++nc;
+                }
+            }
+            if (nc > cap_core || np > cap_pool) {
+#pragma omp atomic write
+                status = ORC_EOVERFLOW;
+            } else {
+                sort_row(core + (size_t)i * cap_core, nc, &g, cells3, u, i, scratch);
+                sort_row(pool + (size_t)i * cap_pool, np, &g, cells3, u, i, scratch);
+            }
+            n_core[i] = nc;
+            n_pool[i] = np;
+        }
+        free(scratch);
+    }
+    free(u);
+    free(cells3);
+    return status;
+}
