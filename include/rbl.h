@@ -63,6 +63,19 @@ typedef enum {
 
 enum { RBL_FP64 = 0, RBL_FP32 = 1 };
 
+/* Where the shell batch is drawn from (Sec. 2):
+ *  RBL_SAMPLE_SHELL   (default) the shell list, j with max(r_c - skin, 0) <= r <
+ *                     r_s + skin at the last build; scale N_s / p.  Cells of width
+ *                     >= (r_s + skin) / K, stencil (2K + 1)^3.
+ *  RBL_SAMPLE_STENCIL the paper's own pool: every other particle of the
+ *                     (2 floor(r_s / r_c) + 3)^3 stencil of cells of edge >= r_c + skin
+ *                     around the particle's cell; scale N_I / p.  No shell list is
+ *                     built (the core list comes from the 27 nearest cells), but only
+ *                     about one draw in ten lands in the shell, so the estimator's
+ *                     variance is larger at the same p.  Needs r_s / r_c < 3 and
+ *                     full_list = 0; cells_per_cutoff is not used. */
+enum { RBL_SAMPLE_SHELL = 0, RBL_SAMPLE_STENCIL = 1 };
+
 typedef struct {
     double L[3];          /* periodic box lengths; each >= 2 (r_s + skin) */
     double r_c;           /* core radius: pairs r < r_c summed directly (Eq. (3)) */
@@ -85,6 +98,7 @@ typedef struct {
                              0 = the mean density N/V.  Set it to the densest
                              region's density for inhomogeneous systems (a liquid
                              slab in vapour), else rows overflow (RBL_EOVERFLOW). */
+    int sampling;         /* RBL_SAMPLE_SHELL (default) or RBL_SAMPLE_STENCIL */
 } rbl_params;
 
 typedef struct {

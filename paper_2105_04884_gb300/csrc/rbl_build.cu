@@ -262,6 +262,14 @@ __global__ void k_copy_back(View v, int conditional)
     v.ubuild[k] = p;
 }
 
+// Offset o along axis a is within one cell of the home cell: offsets -m..m relative
+// to it, or (fewer than 2m + 1 cells) every cell once, offsets 0..n-1.
+__device__ __forceinline__ bool near_offset(const Box &b, int a, int o)
+{
+    if (b.ofs[a][0] < 0) return o >= -1 && o <= 1;
+    return o <= 1 || o == b.n[a] - 1;
+}
+
 // K3: two-level lists (or the full list).  One warp per home cell: the warp walks
 // the cell's candidate sequence 32 candidates at a time (one per lane, fetched
 // once) and tests each against every particle of the cell:
@@ -270,7 +278,10 @@ __global__ void k_copy_back(View v, int conditional)
 //   full : r2 <  (r_s + skin)^2   (full_list mode, in the mask)
 // Candidates are visited in canonical order, so list order and bit order are the
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
-// k.  Row lengths are counted past the core capacity.
+// k.  Row lengths are counted past the core capacity.  With stencil-pool sampling
+// (the paper's own pool) only the core row is built, from the 27 cells around the
+// home cell, and a particle's pool size is its home cell's stencil population less
+// itself; the segment table still spans the whole stencil, for the batch.
 constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
 __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int conditional)
@@ -280,6 +291,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     __shared__ int s_a[kMaxBuildWarps][kMaxSeg], s_la[kMaxBuildWarps][kMaxSeg], s_b[kMaxBuildWarps][kMaxSeg];
     __shared__ int4 s_pos[kMaxBuildWarps][32];
     __shared__ int s_j[kMaxBuildWarps][32];
+    __shared__ int s_nseg[kMaxBuildWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= v.ncell) return; // whole warp; no block-wide barrier below
@@ -331,7 +343,8 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     // next build, however far the particle drifts meanwhile
     for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
     RepScalars &rsc = v.rs[r];
-    if (M > v.Mcap) {
+    const bool pool = v.sampling != 0; // no masks: the stencil population is not bounded by them
+    if (!pool && M > v.Mcap) {
         // too many candidates for the masks: flag it and leave these particles with
         // empty rows so that no kernel decodes a mask that was not written
         for (int i = s0 + lane; i < s1; i += 32) {
@@ -345,7 +358,36 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
         return;
     }
     const float h[3] = {b.h[0], b.h[1], b.h[2]};
-    const int nchunk = (M + 31) >> 5;
+    // Stencil-pool sampling: no shell rows; the core row comes from the cells within
+    // one cell of the home cell (the cell edge is at least r_c + skin), taken in the
+    // order they have in the full stencil, one single-cell segment each.
+    int Sseg = S, Mloop = M;
+    if (pool) {
+        __syncwarp();
+        if (lane == 0) {
+            int ns = 0;
+            pre[0] = 0;
+            for (int sg = 0; sg < S; ++sg) {
+                const int oz = sg / nofs1, oy = sg - oz * nofs1;
+                if (!near_offset(b, 2, b.ofs[2][oz]) || !near_offset(b, 1, b.ofs[1][oy])) continue;
+                const int rowbase = b.c0 + (wrap_cell(cz + b.ofs[2][oz], n2) * n1 + wrap_cell(cy + b.ofs[1][oy], n1)) * n0;
+                for (int k = 0; k < nofs0; ++k) {
+                    if (!near_offset(b, 0, b.ofs[0][k])) continue;
+                    const int cell = rowbase + wrap_cell(cx + b.ofs[0][k], n0);
+                    sA[ns] = v.start[cell];
+                    lA[ns] = v.start[cell + 1] - sA[ns];
+                    sB[ns] = 0;
+                    pre[ns + 1] = pre[ns] + lA[ns];
+                    ++ns;
+                }
+            }
+            s_nseg[warp] = ns;
+        }
+        __syncwarp();
+        Sseg = s_nseg[warp];
+        Mloop = pre[Sseg];
+    }
+    const int nchunk = (Mloop + 31) >> 5;
     const bool full = v.full_list != 0;
     const size_t N = (size_t)v.N;
     int wmc = 0, wms = 0;
@@ -359,9 +401,9 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
         int seg = 0;
         for (int k = 0; k < nchunk; ++k) {
             const int cand = (k << 5) + lane;
-            const bool valid = cand < M;
+            const bool valid = cand < Mloop;
             int sg = seg;
-            while (sg + 1 < S && pre[sg + 1] <= cand) ++sg;
+            while (sg + 1 < Sseg && pre[sg + 1] <= cand) ++sg;
             const int off = cand - pre[sg];
             const int j = off < lA[sg] ? sA[sg] + off : sB[sg] + (off - lA[sg]);
             const int4 pj = valid ? v.pos[j] : make_int4(0, 0, 0, 0);
@@ -377,6 +419,9 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
                 if (full) {
                     in_core = false;
                     in_shell = other && g.r2 < v.t_cut_list;
+                } else if (pool) {
+                    in_core = other && g.r2 < v.t_core_list;
+                    in_shell = false;
                 } else {
                     in_core = other && g.r2 < v.t_core_list;
                     in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
@@ -388,7 +433,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             }
             __syncwarp();
             if (lane < mm) {
-                v.mask[(size_t)k * N + i_me] = my_shell; // coalesced across lanes
+                if (!pool) v.mask[(size_t)k * N + i_me] = my_shell; // coalesced across lanes
                 my_ns += __popc(my_shell);
                 while (my_core) { // core row in candidate order
                     const int b = __ffs(my_core) - 1;
@@ -400,6 +445,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             __syncwarp();
         }
         if (lane < mm) {
+            if (pool) my_ns = M - 1; // the pool: every other particle of the stencil
             v.n_core[i_me] = my_nc;
             v.n_shell[i_me] = my_ns;
             if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);

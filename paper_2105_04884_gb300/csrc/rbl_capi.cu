@@ -80,6 +80,13 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
         if (!(p->L[a] >= 2.0 * (p->r_s + p->skin)))
             BAD("box length L[%d]=%g is below 2 (r_s + skin) = %g", a, p->L[a], 2.0 * (p->r_s + p->skin));
     if (p->cap_core < 0 || p->cap_stencil < 0 || !(p->rho_cap >= 0.0)) BAD("capacities must be >= 0");
+    if (p->sampling != RBL_SAMPLE_SHELL && p->sampling != RBL_SAMPLE_STENCIL)
+        BAD("sampling must be RBL_SAMPLE_SHELL or RBL_SAMPLE_STENCIL");
+    if (p->sampling == RBL_SAMPLE_STENCIL) {
+        if (p->full_list) BAD("stencil-pool sampling is an RBL mode: full_list must be 0");
+        if (2 * ((int)std::floor(p->r_s / p->r_c) + 1) + 1 > kMaxStencil)
+            BAD("stencil-pool sampling needs r_s / r_c < 3 (got %g)", p->r_s / p->r_c);
+    }
     double cells = 1.0;
     for (int a = 0; a < 3; ++a) cells *= std::floor(p->L[a] * p->cells_per_cutoff / (p->r_s + p->skin));
     if (cells > (double)(1 << 28)) BAD("box too large: %.0f cells", cells);
@@ -98,7 +105,8 @@ rbl_status validate_batch(const rbl_params *prm, int R, const int *N, char *err,
         if (a.r_c != b.r_c || a.r_s != b.r_s || a.skin != b.skin || a.p != b.p || a.dt != b.dt ||
             a.gamma != b.gamma || a.precision != b.precision || a.full_list != b.full_list ||
             a.subtract_net_force != b.subtract_net_force || a.cells_per_cutoff != b.cells_per_cutoff ||
-            a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil || a.rho_cap != b.rho_cap)
+            a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil || a.rho_cap != b.rho_cap ||
+            a.sampling != b.sampling)
             BAD("replica %d differs from replica 0 in a shared parameter (only L, T, seed may differ)", r);
         slots += round_up_ll(N[r], kTile);
     }
@@ -111,12 +119,15 @@ Geo replica_geo(const rbl_params *p, int N)
 {
     Geo g{};
     const double rho = p->rho_cap > 0.0 ? p->rho_cap : N / (p->L[0] * p->L[1] * p->L[2]);
-    const double rcut = p->r_s + p->skin;
-    const int K = p->cells_per_cutoff;
+    // shell sampling: cells of width >= (r_s + skin) / K, stencil half-width K;
+    // stencil pool: cells of edge >= r_c + skin, half-width floor(r_s / r_c) + 1
+    const bool pool = p->sampling == RBL_SAMPLE_STENCIL;
+    const int K = pool ? (int)std::floor(p->r_s / p->r_c) + 1 : p->cells_per_cutoff;
     long long nc = 1;
     double span = 1.0;
     for (int a = 0; a < 3; ++a) {
-        int n = (int)std::floor(p->L[a] * (double)K / rcut);
+        int n = pool ? (int)std::floor(p->L[a] / (p->r_c + p->skin))
+                     : (int)std::floor(p->L[a] * (double)p->cells_per_cutoff / (p->r_s + p->skin));
         if (n < 1) n = 1;
         g.n3[a] = n;
         g.nofs3[a] = n >= 2 * K + 1 ? 2 * K + 1 : n;
@@ -154,7 +165,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.n_real = n_real;
     P.S = S;
     P.Mcap = round_up(mcap, 32);
-    P.W = P.Mcap / 32;
+    P.W = prm[0].sampling == RBL_SAMPLE_STENCIL ? 0 : P.Mcap / 32; // the stencil pool needs no masks
     P.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
     P.n_scan_blocks = (P.ncell + 2047) / 2048;
     const size_t Nz = (size_t)P.N;
@@ -198,7 +209,7 @@ Box make_box(const rbl_params *p, int N, int first, int c0, int in0)
 {
     Box b{};
     Geo g = replica_geo(p, N);
-    const int K = p->cells_per_cutoff;
+    const int K = p->sampling == RBL_SAMPLE_STENCIL ? (int)std::floor(p->r_s / p->r_c) + 1 : p->cells_per_cutoff;
     for (int a = 0; a < 3; ++a) {
         b.L[a] = p->L[a];
         b.inv[a] = 4294967296.0 / p->L[a];
@@ -237,6 +248,7 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.full_list = prm->full_list ? 1 : 0;
     v.precision = prm->precision;
     v.subtract = prm->subtract_net_force ? 1 : 0;
+    v.sampling = prm->sampling;
     v.force_threads = 128;
     v.build_warps = 4;
     v.ncell = P.ncell;
@@ -733,6 +745,10 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
 {
     if (!ctx || !rows || !counts || (kind != 0 && kind != 1) || cap < 1) return RBL_EINVAL;
     if (kind == 0 && ctx->view.full_list) return RBL_EINVAL;
+    if (kind == 1 && ctx->view.sampling) {
+        set_err(ctx, "stencil-pool sampling builds no shell rows");
+        return RBL_EINVAL;
+    }
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
     st = check_flags(ctx);
@@ -793,6 +809,10 @@ rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, i
 {
     if (!ctx || !which || !rows || !counts || (kind != 0 && kind != 1) || m < 0 || cap < 1) return RBL_EINVAL;
     if (kind == 0 && ctx->view.full_list) return RBL_EINVAL;
+    if (kind == 1 && ctx->view.sampling) {
+        set_err(ctx, "stencil-pool sampling builds no shell rows");
+        return RBL_EINVAL;
+    }
     for (int k = 0; k < m; ++k)
         if (which[k] < 0 || which[k] >= ctx->n_real) {
             set_err(ctx, "row %lld out of range", which[k]);

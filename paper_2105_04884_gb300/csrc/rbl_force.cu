@@ -2,18 +2,19 @@
 // force, and the parity/observable kernels that share their pair rule.
 //
 // One thread per particle (cell order).  Core row: every entry with r < r_c is
-// summed.  Shell row: a Floyd p-subset of row positions is drawn from Philox stream
-// 0 of (seed, step, tag) -- or the whole row when N_s <= p -- sorted, and located in
-// the shell mask by counting set bits; every drawn entry with r_c <= r < r_s
-// contributes s f_ij, s = N_s / p.  The mask words are read column-major, so a warp
-// reads 32 consecutive particles' words in one transaction, and the walk stops at
-// the word holding the last drawn position.
+// summed.  Shell: a Floyd p-subset of positions is drawn from Philox stream 0 of
+// (seed, step, tag) -- or everything when N <= p -- sorted, and each drawn position
+// is mapped to its neighbour: in the shell mask by its rank among the set bits
+// (shell sampling), or directly in the home cell's stencil (the paper's stencil
+// pool).  Every drawn neighbour with r_c <= r < r_s contributes s f_ij, s = N / p.
+// The mask words are read column-major, so a warp reads 32 consecutive particles'
+// words in one transaction.
 //
-// FP32 path: pair arithmetic in binary32, each pair's force (times s) converted
-// exactly to fixed point at scale 2^24 and summed in integers, so the sum does not
-// depend on order or thread mapping; the total force is accumulated with 64-bit
-// integer atomics (exact).  FP64 path: FP64 pair arithmetic from the FP64 positions,
-// per-block partial sums reduced in a fixed order.
+// FP32 path: pair arithmetic in binary32, the core and batch terms summed per
+// particle in binary32 in the canonical order, the total converted once, exactly,
+// to int64 fixed point at scale 2^24, so sums over particles are exact and do not
+// depend on order or thread mapping.  FP64 path: FP64 pair arithmetic from the FP64
+// positions, per-64-thread partial sums reduced in a fixed order.
 #include "rbl_internal.cuh"
 
 namespace rbl {
@@ -151,7 +152,8 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 
 // MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (mask);
 // MODE 2: exact observables -- the core list and every shell (or full) mask entry,
-// unsampled, energy and virial only (no force written, no total force).
+// or every pool member, unsampled, energy and virial only (no force written, no
+// total force); MODE 3: RBL with the batch drawn from the stencil pool.
 // PMAX > 0: batch positions and neighbour indices live in registers (p <= PMAX);
 // PMAX = 0: general path through local arrays (p up to kMaxP).
 //
@@ -192,7 +194,7 @@ __global__ void __maxnreg__(FP32 ? kForceRegs : 128) k_force(View v, int step_of
     if (live) {
         const Box &b = v.box[r];
         const int4 pi = v.pos[i];
-        const int nc = (MODE == 0 || (MODE == 2 && !v.full_list)) ? min(v.n_core[i], v.cap_c) : 0;
+        const int nc = (MODE == 0 || MODE == 3 || (MODE == 2 && !v.full_list)) ? min(v.n_core[i], v.cap_c) : 0;
         const int ns = v.n_shell[i];
         const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
         const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
@@ -321,6 +323,62 @@ __global__ void __maxnreg__(FP32 ? kForceRegs : 128) k_force(View v, int step_of
                 }
             }
         }
+        if (MODE == 3) {
+            // stencil pool: rank t of the pool is candidate t (t + 1 past the particle's
+            // own position) of the home cell's sequence; no masks
+            const int self = pool_self_position(b, tab, i);
+            if (ns > v.p) {
+                s32 = __fdiv_rn((float)ns, (float)v.p);
+                s64 = (double)ns / (double)v.p;
+            }
+            if constexpr (PMAX > 0) {
+                int S[PMAX];
+                const int nb = batch_sorted<PMAX>(b.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                int J[PMAX];
+                const int S_ = v.S;
+                const int top = S_ <= 32 ? 16 : 32;
+#pragma unroll
+                for (int q = 0; q < PMAX; ++q) {
+                    const int tq = min(S[q], max(ns - 1, 0));
+                    const int cand = tq + (tq >= self ? 1 : 0);
+                    int sg = 0;
+#pragma unroll
+                    for (int sw = 32; sw >= 1; sw >>= 1) {
+                        if (sw > top) continue;
+                        const int m2 = sg + sw;
+                        const int end = __ldg(&tab[min(m2, S_) - 1].w);
+                        sg = (m2 <= S_ && end <= cand) ? m2 : sg;
+                    }
+                    const int4 e = __ldg(&tab[min(sg, S_ - 1)]);
+                    J[q] = cand < e.y ? e.x + cand : e.z + cand;
+                }
+#pragma unroll
+                for (int q0 = 0; q0 < PMAX; q0 += kGather) {
+                    if (q0 < nb) {
+                        int jj[kGather];
+#pragma unroll
+                        for (int u = 0; u < kGather; ++u) jj[u] = J[q0 + u];
+                        acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
+                    }
+                }
+            } else {
+                int S[kMaxP];
+                const int nb = floyd_positions(b.seed, step, pi.w, ns, v.p, S, &v.sc->flags);
+                if (ns > v.p) sort_small(S, nb);
+                for (int q0 = 0; q0 < nb; q0 += kGather) {
+                    int jj[kGather];
+#pragma unroll
+                    for (int u = 0; u < kGather; ++u) {
+                        jj[u] = i;
+                        if (q0 + u < nb) {
+                            const int tq = S[q0 + u];
+                            jj[u] = cur.index_of(tq + (tq >= self ? 1 : 0));
+                        }
+                    }
+                    acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
+                }
+            }
+        }
         // core row, kGather at a time
         for (int k0 = 0; k0 < nc; k0 += kGather) {
             int jj[kGather];
@@ -331,7 +389,20 @@ __global__ void __maxnreg__(FP32 ? kForceRegs : 128) k_force(View v, int step_of
             }
             acc.template pairs<kGather>(v, pi, i, jj, nc - k0, 0);
         }
-        if (MODE != 0) {
+        if (MODE == 2 && v.sampling) {
+            // every pool member (the home cell's stencil less the particle itself)
+            const int self = pool_self_position(b, tab, i);
+            const int M = tab[v.S - 1].w;
+            for (int c0 = 0; c0 < M; c0 += kGather) {
+                int jj[kGather];
+#pragma unroll
+                for (int u = 0; u < kGather; ++u) {
+                    const int c = c0 + u;
+                    jj[u] = (c < M && c != self) ? cur.index_of(c) : i;
+                }
+                acc.template pairs<kGather>(v, pi, i, jj, min(kGather, M - c0), 1);
+            }
+        } else if (MODE == 1 || MODE == 2) {
             // every mask entry, kGather members at a time
             int w = 0;
             unsigned word = ns > 0 ? mask_word(0) : 0u;
@@ -510,7 +581,14 @@ __global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
     const int nb = floyd_positions(v.box[r].seed, step, pi.w, ns, v.p, S, &v.sc->flags);
     sort_small(S, nb);
     SegCursor cur;
-    cur.init(v.seg_tab + (size_t)v.hcell[i] * v.S);
+    const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
+    cur.init(tab);
+    if (v.sampling) {
+        const int self = pool_self_position(v.box[r], tab, i);
+        for (int q = 0; q < nb; ++q) out_j[(size_t)i * v.p + q] = cur.index_of(S[q] + (S[q] >= self ? 1 : 0));
+        out_n[i] = nb;
+        return;
+    }
     int q = 0, seen = 0;
     for (int w = 0; q < nb; ++w) {
         const unsigned word = v.mask[(size_t)w * N + i];
@@ -551,7 +629,16 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
         for (int k = 0; k < nc; ++k) count(v.core[(size_t)k * N + i], true);
     }
     SegCursor cur;
-    cur.init(v.seg_tab + (size_t)v.hcell[i] * v.S);
+    const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
+    cur.init(tab);
+    if (v.sampling) {
+        // the stencil pool holds every pair with r < r_s outside the core
+        const int self = pool_self_position(v.box[r], tab, i);
+        const int M = tab[v.S - 1].w;
+        for (int c = 0; c < M; ++c)
+            if (c != self) count(cur.index_of(c), false);
+        return;
+    }
     int left = v.n_shell[i];
     for (int w = 0; left > 0; ++w) {
         unsigned word = v.mask[(size_t)w * N + i];
@@ -617,6 +704,10 @@ cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cud
     if (v.full_list) {
         if (!fp32) return launch_force_p<1, false, true>(v, step_offset, s);
         return energy ? launch_force_p<1, true, true>(v, step_offset, s) : launch_force_p<1, true, false>(v, step_offset, s);
+    }
+    if (v.sampling) {
+        if (!fp32) return launch_force_p<3, false, true>(v, step_offset, s);
+        return energy ? launch_force_p<3, true, true>(v, step_offset, s) : launch_force_p<3, true, false>(v, step_offset, s);
     }
     if (!fp32) return launch_force_p<0, false, true>(v, step_offset, s);
     return energy ? launch_force_p<0, true, true>(v, step_offset, s) : launch_force_p<0, true, false>(v, step_offset, s);

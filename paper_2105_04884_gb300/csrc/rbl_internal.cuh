@@ -96,6 +96,7 @@ struct View {
     int R;                          // replicas
     int ntile;                      // N / kTile
     int p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
+    int sampling;                   // RBL_SAMPLE_SHELL or RBL_SAMPLE_STENCIL
     int force_threads;              // threads per block of the force kernel (64, 128 or 256)
     int build_warps;                // home cells (warps) per block of the list build (2, 4 or 8)
     int ncell;                      // cells of all replicas, pad cells included
@@ -160,6 +161,21 @@ struct SegCursor {
         return cand < e.y ? e.x + cand : e.z + cand;
     }
 };
+
+// Stencil-pool sampling: the particle's own position in its home cell's candidate
+// sequence (the pool is that sequence without it).  The home cell lies in the row
+// of (y, z) offset 0: index m of the offsets -m..m, or 0 when every cell is visited
+// once starting from the home cell.
+__device__ __forceinline__ int pool_self_position(const Box &b, const int4 *tab, int i)
+{
+    const int iz = b.ofs[2][0] < 0 ? -b.ofs[2][0] : 0;
+    const int iy = b.ofs[1][0] < 0 ? -b.ofs[1][0] : 0;
+    const int s = iz * b.nofs[1] + iy;
+    const int4 e = tab[s];
+    const int pre = s > 0 ? tab[s - 1].w : 0;
+    const int candA = i - e.x;
+    return (candA >= pre && candA < e.y) ? candA : i - e.z;
+}
 
 // Position (0..31) of the r-th (0-based) set bit of w; w must have more than r bits.
 __host__ __device__ __forceinline__ int select_bit(unsigned w, int r)

@@ -20,6 +20,7 @@ import numpy as np
 from . import _build
 
 RBL_FP64, RBL_FP32 = 0, 1
+RBL_SAMPLE_SHELL, RBL_SAMPLE_STENCIL = 0, 1
 STATUS = {0: "RBL_OK", 1: "RBL_EINVAL", 2: "RBL_ENOMEM", 3: "RBL_EOVERFLOW", 4: "RBL_ENONFINITE",
           5: "RBL_ETIMEOUT", 6: "RBL_ECUDA"}
 
@@ -36,7 +37,7 @@ class rbl_params(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int),
                 ("full_list", ctypes.c_int), ("subtract_net_force", ctypes.c_int),
                 ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_stencil", ctypes.c_int),
-                ("rho_cap", ctypes.c_double)]
+                ("rho_cap", ctypes.c_double), ("sampling", ctypes.c_int)]
 
 
 class rbl_obs(ctypes.Structure):
@@ -117,7 +118,8 @@ def load(build_if_missing: bool = False):
 
 
 def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32, full_list=False,
-                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, rho_cap=0.0) -> rbl_params:
+                subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, rho_cap=0.0,
+                sampling=RBL_SAMPLE_SHELL) -> rbl_params:
     prm = rbl_params()
     load().rbl_params_default(ctypes.byref(prm))
     Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
@@ -131,6 +133,7 @@ def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RB
     prm.cells_per_cutoff = int(cells_per_cutoff)
     prm.cap_core, prm.cap_stencil = int(cap_core), int(cap_stencil)
     prm.rho_cap = float(rho_cap)
+    prm.sampling = int(sampling)
     return prm
 
 
@@ -306,10 +309,10 @@ class System(_Context):
 
     def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
                  full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
-                 stream=None, device=None, rho_cap=0.0):
+                 stream=None, device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
         prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
-                          cells_per_cutoff, cap_core, cap_stencil, rho_cap)
+                          cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling)
         self._create([prm], [int(x.shape[0])], stream, device)
         self.set_state(x, v, step)
 
@@ -348,9 +351,10 @@ class Ensemble(_Context):
 
     def __init__(self, replicas, r_c, r_s, skin, p, dt, gamma=0.0, precision=RBL_FP32, full_list=False,
                  subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0, stream=None,
-                 device=None, rho_cap=0.0):
+                 device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL):
         prms = [make_params(rp.L, r_c, r_s, skin, p, dt, rp.T, gamma, rp.seed, precision, full_list,
-                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil, rho_cap) for rp in replicas]
+                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling)
+                for rp in replicas]
         self._create(prms, [len(rp.x) for rp in replicas], stream, device)
         self.offsets = np.concatenate([[0], np.cumsum(self.Ns)])
         x = np.concatenate([rp.x for rp in replicas])
