@@ -152,7 +152,7 @@ PHYS = dict(N=32000, rho=0.8442, T=1.2, rs=3.5, skin=0.3, dt=0.005, gamma=1.0, K
             block=500, stride=10, rdf_every=5, dr=0.02)
 
 
-def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS):
+def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS, sampling=0):
     """Block-averaged observables of one NVT trajectory.  Pressure and energy are the
     exact (unsampled) ones of the configurations the dynamics visits: P = rho T_kin +
     W / (3V) and U / N with W, U over every pair with r < r_s; the RBL estimates of the
@@ -165,7 +165,8 @@ def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS):
     V = float(np.prod(L))
     rho = N / V
     s = rbl.System(x, v, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
-                   gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision, full_list=full)
+                   gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision, full_list=full,
+                   sampling=0 if full else sampling)
     nbins = int(round(cfg["rs"] / cfg["dr"]))
     s.step(cfg["discard"])
     nblk = (cfg["steps"] - cfg["discard"]) // cfg["block"]
@@ -352,16 +353,18 @@ def physics_inputs(seed=1, cfg=PHYS):
     return x, v, L
 
 
-def matched_physics_pair(rc=1.5, p=10, cfg=PHYS, full=None):
-    """RBL (FP32, r_c, p) against the full list (FP32) on the same start."""
+def matched_physics_pair(rc=1.5, p=10, cfg=PHYS, full=None, sampling=0):
+    """RBL (FP32, r_c, p; shell list or stencil pool) against the full list (FP32)
+    on the same start."""
     from paper_2105_04884_gb300 import rbl
 
     x, v, L = physics_inputs(cfg=cfg)
-    a = physics_run(x, v, L, rc, p, rbl.RBL_FP32, False, 1, cfg)
+    a = physics_run(x, v, L, rc, p, rbl.RBL_FP32, False, 1, cfg, sampling=sampling)
     b = full if full is not None else physics_run(x, v, L, rc, p, rbl.RBL_FP32, True, 1, cfg)
     res = physics_compare(a, b, cfg["dr"])
     res["workload"] = "lj_fluid_N32000_rho0.8442_T1.2_rs3.5_nvt"
     res["r_c"], res["p"] = rc, p
+    res["sampling"] = "stencil_pool" if sampling else "shell_list"
     res["steps"], res["discard"], res["block"] = cfg["steps"], cfg["discard"], cfg["block"]
     res["P_est_rbl"] = a["P_est"]
     res["U_est_rbl"] = a["U_est"]
@@ -386,6 +389,15 @@ def physics_sweep():
                 r = physics_run(x, v, L, rc, p, prec, False, 1)
                 c = physics_compare(r, ref, PHYS["dr"])
                 c.update({"precision": name, "method": "rbl", "r_c": rc, "p": p, "P_est": r["P_est"],
+                          "U_est": r["U_est"], "wall_s": r["wall_s"], "n_rebuild": r["n_rebuild"],
+                          "heating": dict(r["heating"], dT_measured=r["T"][0] - ref["T"][0])})
+                print(json.dumps(c), flush=True)
+        # the paper's own pool (every particle of the cell stencil), same comparison
+        for rc in (1.2, 1.5, 2.0):
+            for p in (10, 20):
+                r = physics_run(x, v, L, rc, p, prec, False, 1, sampling=rbl.RBL_SAMPLE_STENCIL)
+                c = physics_compare(r, ref, PHYS["dr"])
+                c.update({"precision": name, "method": "rbl_stencil_pool", "r_c": rc, "p": p, "P_est": r["P_est"],
                           "U_est": r["U_est"], "wall_s": r["wall_s"], "n_rebuild": r["n_rebuild"],
                           "heating": dict(r["heating"], dT_measured=r["T"][0] - ref["T"][0])})
                 print(json.dumps(c), flush=True)
@@ -529,6 +541,21 @@ def run_ours(a, rank, world, local):
                                "speedup_vs_full_list": v2 / vf}
         del s2
         torch.cuda.empty_cache()
+        # the paper's own sampling pool on the same workload: no shell list (the list
+        # build tests only the 27 nearest cells), batch from the whole cell stencil
+        s3 = rbl.System(x, v, L, **dict(common, sampling=rbl.RBL_SAMPLE_STENCIL))
+        s3.step(a.warmup)
+        s3.autotune(trials=3)
+        ms3, (pm3, n3) = timed(s3, a.steps, phases=True)
+        o3 = s3.observables()
+        v3 = N * a.steps * world / (ms3 * 1e-3)
+        result["rbl_stencil_pool"] = {"value": v3, "ms_per_step": ms3 / a.steps,
+                                      "phases_ms_per_step": {"integrate": pm3[0] / n3, "rebuild_chain": pm3[1] / n3,
+                                                             "force_kernel": pm3[2] / n3, "force_reduce": pm3[3] / n3},
+                                      "pool_mean": o3["Ns_mean"], "speedup_vs_full_list": v3 / vf,
+                                      "speedup_vs_shell_list": v3 / value}
+        del s3
+        torch.cuda.empty_cache()
     # end to end through the C ABI with host buffers: upload once, K x (step + scalar
     # readback), download the final state
     if not a.no_e2e:
@@ -570,7 +597,9 @@ def run_ours(a, rank, world, local):
         # against one full-list trajectory
         mp, full_run = matched_physics_pair(1.5, 10)
         mp2, _ = matched_physics_pair(2.0, 10, full=full_run)
-        result["matched_physics"] = [mp, mp2]
+        mp3, _ = matched_physics_pair(1.5, 10, full=full_run, sampling=1)
+        mp4, _ = matched_physics_pair(2.0, 10, full=full_run, sampling=1)
+        result["matched_physics"] = [mp, mp2, mp3, mp4]
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(x, v, L, a.cpu_steps)
     if world > 1:

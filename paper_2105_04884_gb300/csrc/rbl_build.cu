@@ -262,14 +262,6 @@ __global__ void k_copy_back(View v, int conditional)
     v.ubuild[k] = p;
 }
 
-// Offset o along axis a is within one cell of the home cell: offsets -m..m relative
-// to it, or (fewer than 2m + 1 cells) every cell once, offsets 0..n-1.
-__device__ __forceinline__ bool near_offset(const Box &b, int a, int o)
-{
-    if (b.ofs[a][0] < 0) return o >= -1 && o <= 1;
-    return o <= 1 || o == b.n[a] - 1;
-}
-
 // K3: two-level lists (or the full list).  One warp per home cell: the warp walks
 // the cell's candidate sequence 32 candidates at a time (one per lane, fetched
 // once) and tests each against every particle of the cell:
@@ -291,7 +283,6 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     __shared__ int s_a[kMaxBuildWarps][kMaxSeg], s_la[kMaxBuildWarps][kMaxSeg], s_b[kMaxBuildWarps][kMaxSeg];
     __shared__ int4 s_pos[kMaxBuildWarps][32];
     __shared__ int s_j[kMaxBuildWarps][32];
-    __shared__ int s_nseg[kMaxBuildWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= v.ncell) return; // whole warp; no block-wide barrier below
@@ -363,29 +354,39 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     // order they have in the full stencil, one single-cell segment each.
     int Sseg = S, Mloop = M;
     if (pool) {
-        __syncwarp();
-        if (lane == 0) {
-            int ns = 0;
-            pre[0] = 0;
-            for (int sg = 0; sg < S; ++sg) {
-                const int oz = sg / nofs1, oy = sg - oz * nofs1;
-                if (!near_offset(b, 2, b.ofs[2][oz]) || !near_offset(b, 1, b.ofs[1][oy])) continue;
-                const int rowbase = b.c0 + (wrap_cell(cz + b.ofs[2][oz], n2) * n1 + wrap_cell(cy + b.ofs[1][oy], n1)) * n0;
-                for (int k = 0; k < nofs0; ++k) {
-                    if (!near_offset(b, 0, b.ofs[0][k])) continue;
-                    const int cell = rowbase + wrap_cell(cx + b.ofs[0][k], n0);
-                    sA[ns] = v.start[cell];
-                    lA[ns] = v.start[cell + 1] - sA[ns];
-                    sB[ns] = 0;
-                    pre[ns + 1] = pre[ns] + lA[ns];
-                    ++ns;
-                }
-            }
-            s_nseg[warp] = ns;
+        // near offsets per axis in the stencil's order: -1, 0, 1 (offsets relative to
+        // the home cell), or 0, 1, n-1 (every cell once from the home cell; fewer
+        // when n < 3); lane k takes near cell k, in z-major order, then one warp scan
+        int nn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nn[a] = b.ofs[a][0] < 0 ? 3 : min(b.n[a], 3);
+        auto near_o = [&](int a, int k) { return b.ofs[a][0] < 0 ? k - 1 : (k < 2 ? k : b.n[a] - 1); };
+        const int nseg = nn[0] * nn[1] * nn[2];
+        int st = 0, len = 0;
+        if (lane < nseg) {
+            const int iz = lane / (nn[1] * nn[0]), iy = (lane / nn[0]) % nn[1], ix = lane % nn[0];
+            const int cell = b.c0 + (wrap_cell(cz + near_o(2, iz), n2) * n1 + wrap_cell(cy + near_o(1, iy), n1)) * n0 +
+                             wrap_cell(cx + near_o(0, ix), n0);
+            st = v.start[cell];
+            len = v.start[cell + 1] - st;
         }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp(); // every lane is done with the full-stencil segments
+        if (lane < nseg) {
+            sA[lane] = st;
+            lA[lane] = len;
+            sB[lane] = 0;
+            pre[lane + 1] = incl;
+        }
+        if (lane == 0) pre[0] = 0;
         __syncwarp();
-        Sseg = s_nseg[warp];
-        Mloop = pre[Sseg];
+        Sseg = nseg;
+        Mloop = pre[nseg];
     }
     const int nchunk = (Mloop + 31) >> 5;
     const bool full = v.full_list != 0;
