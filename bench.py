@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
     ap.add_argument("--no-slab", action="store_true", help="skip the liquid-vapour slab block")
     ap.add_argument("--ensemble-steps", type=int, default=200)
+    ap.add_argument("--table1", action="store_true",
+                    help="run the paper's Table 1 study (g(r) first peak and MSD slope, classical cutoffs vs RBL)")
+    ap.add_argument("--table1-scale", type=float, default=1.0, help="fraction of the paper's step counts")
     ap.add_argument("--physics", action="store_true",
                     help="run the full matched-physics sweep (r_c x p x precision vs the full list) instead")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="override particle count (debug only)")
@@ -403,6 +406,80 @@ def physics_sweep():
                 print(json.dumps(c), flush=True)
 
 
+# The paper's Table 1 study (Sec. 3): N = 2000, rho* = 0.2, T* = 0.9 (gas-liquid
+# coexistence), tau = 0.002, Langevin gamma = 1, 2x10^5 equilibration and 10^5
+# production steps, 10 runs; g(r) first peak and MSD slope for classical cutoffs
+# r_s = 6, 3, 2 and for RBL with r_s = 6, r_c = 2, p = 10, 20, 50, 100.  The ten
+# runs are one ensemble of ten replicas (seeds 100..109).
+TABLE1 = dict(N=2000, rho=0.2, T=0.9, dt=0.002, gamma=1.0, skin=0.3, runs=10, equil=200000, prod=100000,
+              stride=100, rdf_every=10, dr=0.02, rmax=1.98)
+TABLE1_PAPER = {  # Table 1 of the paper: (g(r) first peak, MSD slope)
+    "DT r_s=6": (7.0196, 2.1117), "DT r_s=3": (6.1095, 2.4668), "DT r_s=2": (2.6592, 3.7144),
+    "RBL p=10": (7.1532, 2.2367), "RBL p=20": (7.0849, 2.0303), "RBL p=50": (7.0366, 2.1669),
+    "RBL p=100": (7.0141, 2.1348)}
+
+
+def table1_study(scale=1.0):
+    import numpy as np
+
+    from paper_2105_04884_gb300 import inputs, rbl
+
+    c = TABLE1
+    reps = []
+    for r in range(c["runs"]):
+        x, L = inputs.fcc(c["N"], c["rho"], 0.01, seed=100 + r)
+        v = inputs.maxwell_boltzmann(c["N"], c["T"], seed=100 + r)
+        reps.append(rbl.Replica(x, v, L, c["T"], 100 + r))
+    L = reps[0].L
+    V = float(np.prod(L))
+    rho = c["N"] / V
+    nb = int(round(c["rmax"] / c["dr"]))
+    shell = 4.0 / 3.0 * math.pi * (np.arange(1, nb + 1) ** 3 - np.arange(nb) ** 3) * c["dr"] ** 3
+    configs = [("DT r_s=6", dict(full_list=True, r_c=1.0, r_s=6.0, p=10)),
+               ("DT r_s=3", dict(full_list=True, r_c=1.0, r_s=3.0, p=10)),
+               ("DT r_s=2", dict(full_list=True, r_c=1.0, r_s=2.0, p=10))]
+    configs += [(f"RBL p={p}", dict(full_list=False, r_c=2.0, r_s=6.0, p=p)) for p in (10, 20, 50, 100)]
+    n_eq = int(c["equil"] * scale)
+    n_pr = int(c["prod"] * scale) // c["stride"] * c["stride"]
+    for name, cfg in configs:
+        t0 = time.perf_counter()
+        # the gas condenses into liquid droplets (rho* ~ 0.75): size the rows for them
+        ens = rbl.Ensemble(reps, skin=c["skin"], dt=c["dt"], gamma=c["gamma"], precision=rbl.RBL_FP32,
+                           rho_cap=0.8, **cfg)
+        ens.step(n_eq)
+        x0 = ens.get_state()[0]
+        prev, unwrapped = x0.copy(), x0.copy()
+        hist = np.zeros((c["runs"], nb), np.int64)
+        nrdf = 0
+        msd = []
+        for k in range(n_pr // c["stride"]):
+            ens.step(c["stride"])
+            x = ens.get_state()[0]
+            d = x - prev
+            d -= L * np.round(d / L)
+            unwrapped += d
+            prev = x
+            disp = ((unwrapped - x0) ** 2).sum(axis=1).reshape(c["runs"], c["N"]).mean(axis=1)
+            msd.append(disp)
+            if (k + 1) % c["rdf_every"] == 0:
+                ens.rdf(c["dr"], nb, hist)
+                nrdf += 1
+        msd = np.asarray(msd)                                 # [samples][runs]
+        t = (np.arange(1, len(msd) + 1) * c["stride"]) * c["dt"]
+        keep = t >= 0.1 * t[-1]                               # past the ballistic start
+        slopes = np.array([np.polyfit(t[keep], msd[keep, r], 1)[0] for r in range(c["runs"])])
+        g = hist / (nrdf * c["N"] * rho * shell)              # [runs][bins]
+        peaks = g.max(axis=1)
+        out = {"config": name, "runs": c["runs"], "equil_steps": n_eq, "prod_steps": n_pr,
+               "g_peak": [float(peaks.mean()), float(peaks.std(ddof=1) / math.sqrt(c["runs"]))],
+               "g_peak_r": float((np.argmax(g.mean(axis=0)) + 0.5) * c["dr"]),
+               "msd_slope": [float(slopes.mean()), float(slopes.std(ddof=1) / math.sqrt(c["runs"]))],
+               "paper_g_peak": TABLE1_PAPER[name][0], "paper_msd_slope": TABLE1_PAPER[name][1],
+               "wall_s": time.perf_counter() - t0}
+        print(json.dumps(out), flush=True)
+        del ens
+
+
 def make_workload(N, seed):
     from paper_2105_04884_gb300 import inputs
 
@@ -677,6 +754,10 @@ def main():
     if a.physics:
         if rank == 0:
             physics_sweep()
+        return
+    if a.table1:
+        if rank == 0:
+            table1_study(a.table1_scale)
         return
     if a.impl == "reference":
         res = run_reference(a, rank, world)

@@ -81,7 +81,7 @@ typedef struct {
     double r_c;           /* core radius: pairs r < r_c summed directly (Eq. (3)) */
     double r_s;           /* cutoff radius: pairs r_c <= r < r_s sampled (Eq. (4)) */
     double skin;          /* Verlet skin; lists rebuilt when a particle moved > skin/2 */
-    int p;                /* batch size, 1 <= p <= 64 */
+    int p;                /* batch size, 1 <= p <= 128 */
     double dt;            /* time step */
     double T;             /* bath temperature (k_B T) */
     double gamma;         /* Langevin friction; 0 = plain velocity-Verlet (NVE) */
@@ -128,7 +128,7 @@ void rbl_params_default(rbl_params *prm);
 rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes);
 
 /* Creates a context (host memory for the handle only).  Validates: N >= 2,
- * 0 < r_c < r_s, skin >= 0, 1 <= p <= 64, dt > 0, T >= 0, gamma >= 0, finite values,
+ * 0 < r_c < r_s, skin >= 0, 1 <= p <= 128, dt > 0, T >= 0, gamma >= 0, finite values,
  * every L_a >= 2 (r_s + skin), K in 1..3.  stream is a cudaStream_t (or NULL).
  * The initial state is zero; load one with rbl_set_state. */
 rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,

@@ -14,7 +14,7 @@
 
 namespace rbl {
 
-constexpr int kMaxP = 64;          // largest batch size
+constexpr int kMaxP = 128;         // largest batch size
 constexpr int kCellCap = 64;       // cells up to this size are sorted in local memory
 constexpr int kBlock = 256;        // threads per block of the per-particle kernels
 constexpr int kMinBlock = 64;      // smallest per-particle block: sizes the per-block partials

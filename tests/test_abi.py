@@ -57,7 +57,7 @@ def test_workspace_size_and_validation(lib):
     assert st == 0 and n2 > n1
     bad = [
         dict(r_c=3.5, r_s=1.5),                 # r_c >= r_s
-        dict(p=0), dict(p=65),                  # batch size range
+        dict(p=0), dict(p=129),                 # batch size range
         dict(dt=0.0), dict(skin=-0.1),
         dict(L=[7.0, 10.772, 10.772]),          # box below 2 (r_s + skin)
         dict(cells_per_cutoff=4),

@@ -34,6 +34,8 @@ CASES = {
     "n3000_rc2_K3": dict(N=3000, rho=0.7, jitter=0.3, rc=2.0, rs=3.5, skin=0.3, p=20, K=3, seed=5),
     # p = 1
     "n2000_p1": dict(N=2000, rho=0.8, jitter=0.3, rc=1.5, rs=3.5, skin=0.3, p=1, K=2, seed=6),
+    # the paper's Table 1 system: dilute, r_s = 6, r_c = 2, p = 100 (general batch path)
+    "n2000_rho0.2_rs6_p100": dict(N=2000, rho=0.2, jitter=0.3, rc=2.0, rs=6.0, skin=0.3, p=100, K=2, seed=7),
 }
 
 
