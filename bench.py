@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
     ap.add_argument("--no-slab", action="store_true", help="skip the liquid-vapour slab block")
     ap.add_argument("--ensemble-steps", type=int, default=200)
+    ap.add_argument("--variance", action="store_true",
+                    help="run the force-error variance study against the paper's Appendix A estimate")
     ap.add_argument("--table1", action="store_true",
                     help="run the paper's Table 1 study (g(r) first peak and MSD slope, classical cutoffs vs RBL)")
     ap.add_argument("--table1-scale", type=float, default=1.0, help="fraction of the paper's step counts")
@@ -480,6 +482,54 @@ def table1_study(scale=1.0):
         del ens
 
 
+def variance_study(draws=8):
+    """Variance of the force error chi_i = F~_i - F_i (Appendix A) on one equilibrated
+    liquid configuration (the matched-physics system: N = 32,000, rho* = 0.8442,
+    T* = 1.2, r_s = 3.5), for r_c in {1.2, 1.5, 2.0, 2.5}, p in {5, 10, 20} and both
+    pools, over `draws` independent batches (different step counters), FP64.  Beside
+    the measurement: Appendix A's leading term (N - p)/p * int_{r_c}^{r_s} 4 pi rho r^2
+    f(r)^2 dr with N the mean pool (N_s or N_I) and g = 1 as the paper assumes, and the
+    same integral weighted by the measured g(r)."""
+    import numpy as np
+
+    from paper_2105_04884_gb300 import rbl
+
+    cfg = PHYS
+    x, v, L = physics_inputs()
+    rho = len(x) / float(np.prod(L))
+    eq = rbl.System(x, v, L, r_c=1.5, r_s=cfg["rs"], skin=cfg["skin"], p=10, dt=cfg["dt"], T=cfg["T"],
+                    gamma=cfg["gamma"], seed=1, full_list=True, precision=rbl.RBL_FP64)
+    eq.step(2000)
+    xs, vs, _ = eq.get_state()
+    F_full = eq.forces()
+    dr = 0.01
+    nb = int(round(cfg["rs"] / dr)) - 1
+    h = eq.rdf(dr, nb)
+    r = (np.arange(nb) + 0.5) * dr
+    g = h / (len(x) * rho * 4.0 / 3.0 * np.pi * ((r + dr / 2) ** 3 - (r - dr / 2) ** 3))
+    f2 = (24.0 * (2.0 * r ** -13 - r ** -7)) ** 2
+    del eq
+    for mode, name in ((rbl.RBL_SAMPLE_SHELL, "shell_list"), (rbl.RBL_SAMPLE_STENCIL, "stencil_pool")):
+        for rc in (1.2, 1.5, 2.0, 2.5):
+            for p in (5, 10, 20):
+                s = rbl.System(xs, vs, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
+                               gamma=cfg["gamma"], seed=7, precision=rbl.RBL_FP64, sampling=mode)
+                acc = 0.0
+                for k in range(draws):
+                    s.set_state(xs, vs, step=1000 + k)
+                    acc += float(np.mean(np.sum((s.forces() - F_full) ** 2, axis=1)))
+                meas = acc / draws
+                npool = s.observables()["Ns_mean"]
+                win = (r >= rc) & (r < cfg["rs"])
+                integ = np.sum(4.0 * np.pi * rho * r[win] ** 2 * f2[win]) * dr
+                integ_g = np.sum(4.0 * np.pi * rho * r[win] ** 2 * g[win] * f2[win]) * dr
+                fac = (npool - p) / p
+                print(json.dumps({"sampling": name, "r_c": rc, "p": p, "pool_mean": npool, "var_chi": meas,
+                                  "appendix_g1": fac * integ, "appendix_with_g": fac * integ_g,
+                                  "ratio_meas_over_g": meas / (fac * integ_g)}), flush=True)
+                del s
+
+
 def make_workload(N, seed):
     from paper_2105_04884_gb300 import inputs
 
@@ -758,6 +808,10 @@ def main():
     if a.table1:
         if rank == 0:
             table1_study(a.table1_scale)
+        return
+    if a.variance:
+        if rank == 0:
+            variance_study()
         return
     if a.impl == "reference":
         res = run_reference(a, rank, world)
