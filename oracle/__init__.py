@@ -77,17 +77,18 @@ def _declare(L):
     L.orc_build_lists_cells.argtypes = sig_lists
     L.orc_build_lists_cells.restype = I
     L.orc_lj.argtypes = [I, P, P, P]
-    L.orc_rbl_forces.argtypes = [I, P, P, D, D, D, I, U64, U64, P, P, I, P, P, I, P, P, P, P]
+    L.orc_pair.argtypes = [I, P, D, D, P, P]
+    L.orc_rbl_forces.argtypes = [I, P, P, D, D, D, I, U64, U64, P, P, I, P, P, I, P, P, P, P, P, D]
     L.orc_rbl_forces.restype = I
     L.orc_build_pool.argtypes = [I, P, P, D, D, D, I, I, P, P, P, P, P]
     L.orc_build_pool.restype = I
-    L.orc_sample.argtypes = [I, P, P, D, D, D, I, I, U64, U64, I, P, I, I, P, P, P, P, P, P, P]
+    L.orc_sample.argtypes = [I, P, P, D, D, D, I, I, U64, U64, I, P, I, I, P, P, P, P, P, P, P, P, D]
     L.orc_sample.restype = I
-    L.orc_full_forces.argtypes = [I, P, P, D, P, P, I, P, P]
+    L.orc_full_forces.argtypes = [I, P, P, D, P, P, I, P, P, P, D]
     L.orc_full_forces.restype = I
-    L.orc_brute_forces.argtypes = [I, P, P, D, P, P]
+    L.orc_brute_forces.argtypes = [I, P, P, D, P, P, P, D]
     L.orc_subtract_mean.argtypes = [I, P]
-    L.orc_run.argtypes = [I, P, P, P, P, D, D, D, I, I, D, D, D, U64, U64, I, I, I, I, I, I, P]
+    L.orc_run.argtypes = [I, P, P, P, P, D, D, D, I, I, D, D, D, U64, U64, I, I, I, I, I, I, P, P, D]
     L.orc_run.restype = I
     L.orc_tail.argtypes = [D, D, P]
     L.orc_thermo.argtypes = [I, P, P, D, P]
@@ -219,17 +220,39 @@ def lj(r):
     return u, f
 
 
-def rbl_forces(x, L, rc, rs, skin, p, seed, step, lists, want_batch=False):
-    """F_i = F_i,c + F~_i,s (no mean subtraction); returns (F, (U_est, W_est), batch, batch_n)."""
+def _charges(q, n):
+    """Charges as a contiguous float64 array of n, or None (LJ only)."""
+    if q is None:
+        return None
+    q = _f64(q).reshape(-1)
+    if q.shape[0] != n:
+        raise ValueError("one charge per particle")
+    return q
+
+
+def pair(r, qq=0.0, alpha=0.0):
+    """Energy and radial force magnitude of a pair at distances r: LJ plus, for
+    qq = q_i q_j != 0, the Ewald real-space term qq erfc(alpha r) / r."""
+    r = _f64(r)
+    u = np.zeros_like(r)
+    f = np.zeros_like(r)
+    lib().orc_pair(r.shape[0], _p(r), float(qq), float(alpha), _p(u), _p(f))
+    return u, f
+
+
+def rbl_forces(x, L, rc, rs, skin, p, seed, step, lists, want_batch=False, q=None, alpha=0.0):
+    """F_i = F_i,c + F~_i,s (no mean subtraction); returns (F, (U_est, W_est), batch, batch_n).
+    q: per-particle charges for the LJ + Ewald real-space pair (None: LJ only)."""
     x = _f64(x, (-1, 3))
     n = x.shape[0]
+    q = _charges(q, n)
     F = np.zeros((n, 3))
     ev = np.zeros(2)
     batch = np.full((n, max(p, 1)), -1, np.int32) if want_batch else None
     bn = np.zeros(n, np.int32) if want_batch else None
     lib().orc_rbl_forces(n, _p(x), _p(_f64(L)), rc, rs, skin, p, seed, step, _p(lists.core), _p(lists.n_core),
                          lists.core.shape[1], _p(lists.shell), _p(lists.n_shell), lists.shell.shape[1], _p(F),
-                         _p(ev), _p(batch), _p(bn))
+                         _p(ev), _p(batch), _p(bn), _p(q), float(alpha))
     return F, ev, batch, bn
 
 
@@ -266,11 +289,12 @@ class Sample:
         return arr[k, : cnt[k]]
 
 
-def sample(x, L, rc, rs, skin, p, seed, step, idx, K=2, cap_core=160, cap_shell=640):
+def sample(x, L, rc, rs, skin, p, seed, step, idx, K=2, cap_core=160, cap_shell=640, q=None, alpha=0.0):
     """Core and shell rows (canonical order), batch at `step` and un-subtracted RBL
     force of the particles idx, each computed on its own against all the others."""
     x = _f64(x, (-1, 3))
     n = x.shape[0]
+    q = _charges(q, n)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     m = idx.shape[0]
     core = np.full((m, cap_core), -1, np.int32)
@@ -281,28 +305,30 @@ def sample(x, L, rc, rs, skin, p, seed, step, idx, K=2, cap_core=160, cap_shell=
     nb = np.zeros(m, np.int32)
     F = np.zeros((m, 3))
     st = lib().orc_sample(n, _p(x), _p(_f64(L)), rc, rs, skin, K, p, seed, step, m, _p(idx), cap_core, cap_shell,
-                          _p(core), _p(nc), _p(shell), _p(ns), _p(batch), _p(nb), _p(F))
+                          _p(core), _p(nc), _p(shell), _p(ns), _p(batch), _p(nb), _p(F), _p(q), float(alpha))
     if st != 0:
         raise OverflowError("oracle row exceeded its capacity")
     return Sample(idx, core, nc, shell, ns, batch, nb, F)
 
 
-def full_forces(x, L, rs, lists):
+def full_forces(x, L, rs, lists, q=None, alpha=0.0):
     x = _f64(x, (-1, 3))
     n = x.shape[0]
+    q = _charges(q, n)
     F = np.zeros((n, 3))
     ev = np.zeros(2)
     lib().orc_full_forces(n, _p(x), _p(_f64(L)), rs, _p(lists.full), _p(lists.n_full), lists.full.shape[1],
-                          _p(F), _p(ev))
+                          _p(F), _p(ev), _p(q), float(alpha))
     return F, ev
 
 
-def brute_forces(x, L, rs):
+def brute_forces(x, L, rs, q=None, alpha=0.0):
     x = _f64(x, (-1, 3))
     n = x.shape[0]
+    q = _charges(q, n)
     F = np.zeros((n, 3))
     ev = np.zeros(2)
-    lib().orc_brute_forces(n, _p(x), _p(_f64(L)), rs, _p(F), _p(ev))
+    lib().orc_brute_forces(n, _p(x), _p(_f64(L)), rs, _p(F), _p(ev), _p(q), float(alpha))
     return F, ev
 
 
@@ -322,15 +348,17 @@ def max_threads():
 
 
 def run(x, v, L, rc, rs, skin, p, dt, T, gamma, seed, n_steps, step0=0, K=2, subtract_mean=True,
-        full_list=False, cap_core=160, cap_shell=640, cap_full=640):
+        full_list=False, cap_core=160, cap_shell=640, cap_full=640, q=None, alpha=0.0):
     """Advance (x, v) by n_steps; returns (x, v, F, (U, W, n_rebuild))."""
     x = _f64(x, (-1, 3)).copy()
     v = _f64(v, (-1, 3)).copy()
     n = x.shape[0]
+    q = _charges(q, n)
     F = np.zeros((n, 3))
     stats = np.zeros(3)
     st = lib().orc_run(n, _p(x), _p(v), _p(F), _p(_f64(L)), rc, rs, skin, p, K, dt, T, gamma, seed, step0,
-                       n_steps, int(subtract_mean), int(full_list), cap_core, cap_shell, cap_full, _p(stats))
+                       n_steps, int(subtract_mean), int(full_list), cap_core, cap_shell, cap_full, _p(stats),
+                       _p(q), float(alpha))
     if st != 0:
         raise OverflowError("oracle list row exceeded its capacity")
     return x, v, F, stats

@@ -17,8 +17,10 @@
  * Pinned by tests/test_oracle_*.py (closed forms, brute force, invariants,
  * published known-answer vectors).  Functions without a pin say so.
  *
- * Conventions (each is a reading of the paper; all are listed in the design doc):
- *  - reduced LJ units, sigma = epsilon = m = k_B = 1 (Sec. 3).
+ * Conventions (each is a reading of the paper):
+ *  - reduced LJ units, sigma = epsilon = m = k_B = 1 (Sec. 3); charges (the Ewald
+ *    real-space extension) in units where two unit charges at distance r have
+ *    Coulomb energy 1/r.
  *  - positions x[i*3+a] in [0, L_a), periodic, particle index == tag.
  *  - the decision "is r_ij below a cutoff" is taken on a 32-bit fixed-point image
  *    of the positions, in IEEE binary32 (the precision of the GPU kernels), see
@@ -569,6 +571,49 @@ static double lj_pair(const double d[3], double fvec[3], double *virial)
     return 4.0 * (ir6 * ir6 - ir6);
 }
 
+/* Charged pairs: the LJ 12-6 pair plus the Ewald real-space term, the short-range
+ * part of the Coulomb interaction to which the RBL extends unchanged (Sec. 2,
+ * closing remarks; Sec. 4):
+ *   u_C(r) = q_i q_j erfc(alpha r) / r,
+ *   r . f_C = q_i q_j (erfc(alpha r) / r + (2 alpha / sqrt(pi)) exp(-alpha^2 r^2)),
+ * f_C = (r . f_C) / r^2 d_ij.  q == NULL: the LJ pair alone (bit for bit).       */
+typedef struct {
+    const double *q; /* charge of each particle, or NULL */
+    double alpha;    /* Ewald splitting parameter */
+} pair_pot;
+
+static double pot_pair(const pair_pot *pp, int i, int j, const double d[3], double fvec[3], double *virial)
+{
+    if (!pp || !pp->q) return lj_pair(d, fvec, virial);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double ir2 = 1.0 / r2;
+    double ir6 = ir2 * ir2 * ir2;
+    double w = 24.0 * (2.0 * ir6 * ir6 - ir6);
+    double u = 4.0 * (ir6 * ir6 - ir6);
+    double qq = pp->q[i] * pp->q[j];
+    double r = sqrt(r2);
+    double ec = erfc(pp->alpha * r) / r;
+    u += qq * ec;
+    w += qq * (ec + 2.0 * pp->alpha / sqrt(3.14159265358979323846) * exp(-pp->alpha * pp->alpha * r2));
+    double coef = w * ir2;
+    for (int a = 0; a < 3; ++a) fvec[a] = coef * d[a];
+    if (virial) *virial = w;
+    return u;
+}
+
+/* Pair energy and radial force magnitude of two charges q_i q_j = qq at distance
+ * r[k] (qq = 0: the LJ pair). */
+void orc_pair(int n, const double *r, double qq, double alpha, double *u_out, double *fmag_out)
+{
+    const double q2[2] = {1.0, qq};
+    pair_pot pp = {q2, alpha};
+    for (int k = 0; k < n; ++k) {
+        double d[3] = {r[k], 0.0, 0.0}, fv[3];
+        u_out[k] = pot_pair(&pp, 0, 1, d, fv, NULL);
+        fmag_out[k] = fv[0];
+    }
+}
+
 void orc_lj(int n, const double *r, double *u_out, double *fmag_out)
 {
     for (int k = 0; k < n; ++k) {
@@ -595,7 +640,7 @@ void orc_lj(int n, const double *r, double *u_out, double *fmag_out)
  * is the Floyd sample of row positions drawn from Philox stream 0 of (seed, step,
  * tag i).  Also returns this particle's halves of the energy and virial estimates. */
 static void force_one(int i, const double *x, const uint32_t *u, const fixed_frame *f, const thresholds *t,
-                      const double L[3], int p, uint64_t seed, uint64_t step, const int32_t *crow, int nc,
+                      const pair_pot *pp, const double L[3], int p, uint64_t seed, uint64_t step, const int32_t *crow, int nc,
                       const int32_t *srow, int ns, int32_t *pos, double Fi[3], double *e_i, double *w_i,
                       int32_t *batch_out, int32_t *batch_n)
 {
@@ -607,7 +652,7 @@ static void force_one(int i, const double *x, const uint32_t *u, const fixed_fra
         if (!(r2f < t->rc2)) continue;
         double d[3], fv[3], vir;
         min_image(x + 3 * i, x + 3 * j, L, d);
-        ec += lj_pair(d, fv, &vir);
+        ec += pot_pair(pp, i, j, d, fv, &vir);
         wc += vir;
         for (int a = 0; a < 3; ++a) fc[a] += fv[a];
     }
@@ -620,7 +665,7 @@ static void force_one(int i, const double *x, const uint32_t *u, const fixed_fra
         if (!(r2f >= t->rc2 && r2f < t->rs2)) continue;
         double d[3], fv[3], vir;
         min_image(x + 3 * i, x + 3 * j, L, d);
-        es += lj_pair(d, fv, &vir);
+        es += pot_pair(pp, i, j, d, fv, &vir);
         wsum += vir;
         for (int a = 0; a < 3; ++a) fs[a] += fv[a];
     }
@@ -633,8 +678,9 @@ static void force_one(int i, const double *x, const uint32_t *u, const fixed_fra
 int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double rs, double skin, int p,
                    uint64_t seed, uint64_t step, const int32_t *core, const int32_t *n_core, int cap_core,
                    const int32_t *shell, const int32_t *n_shell, int cap_shell, double *F, double *energy_virial,
-                   int32_t *batch_out, int32_t *batch_n)
+                   int32_t *batch_out, int32_t *batch_n, const double *q, double alpha)
 {
+    const pair_pot pp = {q, alpha};
     fixed_frame f;
     frame_init(&f, L);
     thresholds t = make_thresholds(rc, rs, skin);
@@ -648,7 +694,7 @@ int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double 
 #pragma omp for schedule(static)
         for (int i = 0; i < n; ++i) {
             double e_i, w_i;
-            force_one(i, x, u, &f, &t, L, p, seed, step, core + (size_t)i * cap_core, n_core[i],
+            force_one(i, x, u, &f, &t, &pp, L, p, seed, step, core + (size_t)i * cap_core, n_core[i],
                       shell + (size_t)i * cap_shell, n_shell[i], pos, F + 3 * (size_t)i, &e_i, &w_i,
                       batch_out ? batch_out + (size_t)i * p : NULL, batch_n ? batch_n + i : NULL);
             e_tot += e_i;
@@ -674,8 +720,9 @@ int orc_rbl_forces(int n, const double *x, const double L[3], double rc, double 
 int orc_sample(int n, const double *x, const double L[3], double rc, double rs, double skin, int K, int p,
                uint64_t seed, uint64_t step, int m, const int32_t *idx, int cap_core, int cap_shell,
                int32_t *core, int32_t *n_core, int32_t *shell, int32_t *n_shell, int32_t *batch,
-               int32_t *n_batch, double *F)
+               int32_t *n_batch, double *F, const double *q, double alpha)
 {
+    const pair_pot pp = {q, alpha};
     fixed_frame f;
     frame_init(&f, L);
     thresholds t = make_thresholds(rc, rs, skin);
@@ -720,7 +767,7 @@ int orc_sample(int n, const double *x, const double L[3], double rc, double rs, 
             sort_row(crow, nc, &g, cells3, u, i, scratch);
             sort_row(srow, ns, &g, cells3, u, i, scratch);
             double e_i, w_i;
-            force_one(i, x, u, &f, &t, L, p, seed, step, crow, nc, srow, ns, pos, F + 3 * (size_t)k, &e_i,
+            force_one(i, x, u, &f, &t, &pp, L, p, seed, step, crow, nc, srow, ns, pos, F + 3 * (size_t)k, &e_i,
                       &w_i, batch + (size_t)k * p, n_batch + k);
         }
         free(pos);
@@ -734,8 +781,10 @@ int orc_sample(int n, const double *x, const double L[3], double rc, double rs, 
 /* Classical cutoff force from a full Verlet list: sum over full_i with
  * r2 < r_s^2 of f_ij; energy and virial summed over unordered pairs.           */
 int orc_full_forces(int n, const double *x, const double L[3], double rs, const int32_t *full,
-                    const int32_t *n_full, int cap_full, double *F, double *energy_virial)
+                    const int32_t *n_full, int cap_full, double *F, double *energy_virial, const double *q,
+                    double alpha)
 {
+    const pair_pot pp = {q, alpha};
     fixed_frame f;
     frame_init(&f, L);
     float rs2 = (float)(rs * rs);
@@ -753,7 +802,7 @@ int orc_full_forces(int n, const double *x, const double L[3], double rs, const 
             if (!(r2f < rs2)) continue;
             double d[3], fv[3], vir;
             min_image(x + 3 * i, x + 3 * j, L, d);
-            e_tot += 0.5 * lj_pair(d, fv, &vir);
+            e_tot += 0.5 * pot_pair(&pp, i, j, d, fv, &vir);
             w_tot += 0.5 * vir;
             for (int a = 0; a < 3; ++a) fi[a] += fv[a];
         }
@@ -769,8 +818,10 @@ int orc_full_forces(int n, const double *x, const double L[3], double rs, const 
 
 /* All-pairs O(N^2) cutoff force with no lists at all (the definition the lists
  * must reproduce).  Energy and virial over unordered pairs i < j.               */
-void orc_brute_forces(int n, const double *x, const double L[3], double rs, double *F, double *energy_virial)
+void orc_brute_forces(int n, const double *x, const double L[3], double rs, double *F, double *energy_virial,
+                      const double *q, double alpha)
 {
+    const pair_pot pp = {q, alpha};
     fixed_frame f;
     frame_init(&f, L);
     float rs2 = (float)(rs * rs);
@@ -787,7 +838,7 @@ void orc_brute_forces(int n, const double *x, const double L[3], double rs, doub
             if (!(r2f < rs2)) continue;
             double d[3], fv[3], vir;
             min_image(x + 3 * i, x + 3 * j, L, d);
-            double e = lj_pair(d, fv, &vir);
+            double e = pot_pair(&pp, i, j, d, fv, &vir);
             if (j > i) {
                 e_tot += e;
                 w_tot += vir;
@@ -836,6 +887,8 @@ typedef struct {
     int subtract_mean;
     int full_list; /* 1: classical cutoff (no batch) */
     int cap_core, cap_shell, cap_full;
+    const double *q; /* charges (NULL: LJ only) */
+    double alpha;
 } orc_params;
 
 typedef struct {
@@ -881,11 +934,12 @@ static int orc_force_eval(const orc_params *pr, orc_state *s)
 {
     int st;
     if (pr->full_list)
-        st = orc_full_forces(s->n, s->x, pr->L, pr->rs, s->full, s->n_full, pr->cap_full, s->F, s->ev);
+        st = orc_full_forces(s->n, s->x, pr->L, pr->rs, s->full, s->n_full, pr->cap_full, s->F, s->ev, pr->q,
+                             pr->alpha);
     else
         st = orc_rbl_forces(s->n, s->x, pr->L, pr->rc, pr->rs, pr->skin, pr->p, pr->seed, s->step, s->core,
                             s->n_core, pr->cap_core, s->shell, s->n_shell, pr->cap_shell, s->F, s->ev, NULL,
-                            NULL);
+                            NULL, pr->q, pr->alpha);
     if (pr->subtract_mean) orc_subtract_mean(s->n, s->F);
     return st;
 }
@@ -903,7 +957,8 @@ static void wrap(double *x, const double L[3])
  * rebuilds}.  Lists are built at the start.  step0 = counter of the first force. */
 int orc_run(int n, double *x, double *v, double *F_out, const double L[3], double rc, double rs, double skin,
             int p, int K, double dt, double T, double gamma, uint64_t seed, uint64_t step0, int n_steps,
-            int subtract_mean, int full_list, int cap_core, int cap_shell, int cap_full, double *stats_out)
+            int subtract_mean, int full_list, int cap_core, int cap_shell, int cap_full, double *stats_out,
+            const double *q, double alpha)
 {
     orc_params pr;
     memcpy(pr.L, L, sizeof(pr.L));
@@ -911,6 +966,7 @@ int orc_run(int n, double *x, double *v, double *F_out, const double L[3], doubl
     pr.dt = dt; pr.T = T; pr.gamma = gamma; pr.seed = seed;
     pr.subtract_mean = subtract_mean; pr.full_list = full_list;
     pr.cap_core = cap_core; pr.cap_shell = cap_shell; pr.cap_full = cap_full;
+    pr.q = q; pr.alpha = alpha;
     orc_state s;
     s.n = n; s.x = x; s.v = v; s.F = F_out; s.step = step0; s.n_rebuild = 0;
     s.core = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * cap_core);

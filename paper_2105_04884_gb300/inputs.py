@@ -19,6 +19,10 @@ benchmarked at:
 * ``slab(...)``: liquid FCC slab over the central fraction of z plus a uniform vapour.
 * ``ensemble(...)``: independent replicas with log-uniform sizes and uniform densities
   and temperatures.
+* ``charges(N, ...)``: a neutral set of charges +q / -q (half each, one 0 when N is
+  odd) in random order, for the charged LJ fluid of the Ewald real-space workload.
+* ``rock_salt(n, r0)``: the NaCl lattice, n^3 sites of a simple cubic lattice of
+  spacing r0 with alternating unit charges.
 """
 from __future__ import annotations
 
@@ -135,3 +139,25 @@ def ensemble(R: int = 256, n_min: int = 500, n_max: int = 20000, rho=(0.6, 0.9),
         v = maxwell_boltzmann(N, t, seed + r)
         out.append(Replica(N, rh, t, seed + r, x, v, L))
     return out
+
+
+def charges(N: int, q: float = 1.0, seed: int = 1) -> np.ndarray:
+    """Neutral charges: +q on half the particles, -q on the other half (and 0 on one
+    particle when N is odd), in a seeded random order."""
+    out = np.zeros(N, np.float64)
+    h = N // 2
+    out[:h] = q
+    out[h : 2 * h] = -q
+    return out[_rng(seed, 5).permutation(N)]
+
+
+def rock_salt(n: int, r0: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(x, L, q): n^3 sites (n even) of a simple cubic lattice of spacing r0, offset
+    by r0/2 from the box faces, with charge (-1)^(ix + iy + iz)."""
+    if n % 2:
+        raise ValueError("n must be even for a periodic rock-salt lattice")
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    idx = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+    x = (idx + 0.5) * r0
+    q = np.where(idx.sum(axis=1) % 2 == 0, 1.0, -1.0)
+    return np.ascontiguousarray(x, dtype=np.float64), np.full(3, n * r0), q
