@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s, RBL vs full Verlet list on 1 GB300 at matched pressure/g(r)"
 WORKLOAD = dict(name="lj_fluid_N1048576_rho0.8_T1.5_rc1.5_rs3.5_skin0.3_p10_nvt", N=1048576, rho=0.8, T=1.5,
                 rc=1.5, rs=3.5, skin=0.3, p=10, dt=0.005, gamma=1.0, K=2)
-FORCE_KERNEL = "k_force<0, true, false>"  # RBL, FP32, no energy
+FORCE_KERNEL = "k_force<0, true, false, 10, false>"  # RBL, FP32, no energy, p = 10, LJ
+FORCE_KERNEL_EWALD = "k_force<0, true, false, 10, true>"  # the same with the Ewald real-space term
 
 
 def parse():
@@ -49,6 +50,9 @@ def parse():
     ap.add_argument("--no-physics", action="store_true", help="skip the matched-physics block")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
     ap.add_argument("--no-slab", action="store_true", help="skip the liquid-vapour slab block")
+    ap.add_argument("--no-ewald", action="store_true", help="skip the charged-fluid (Ewald real-space) block")
+    ap.add_argument("--potential", default="lj", choices=["lj", "ewald"],
+                    help="pair kernel of the timed workload: LJ, or LJ + Ewald real-space on the charged fluid")
     ap.add_argument("--ensemble-steps", type=int, default=200)
     ap.add_argument("--variance", action="store_true",
                     help="run the force-error variance study against the paper's Appendix A estimate")
@@ -530,6 +534,34 @@ def variance_study(draws=8):
                 del s
 
 
+EWALD_ALPHA = 1.0  # erfc(alpha r_s) = 7e-7 at r_s = 3.5
+
+
+def ewald_bench(a, world, x, v, L, common, timed):
+    """The Ewald real-space extension on the headline workload's positions: the same
+    fluid with neutral random +-1 charges, pair LJ + q_i q_j erfc(alpha r) / r; RBL
+    against the full list, both autotuned."""
+    import torch
+
+    from paper_2105_04884_gb300 import inputs, rbl
+
+    N = len(x)
+    q = inputs.charges(N, 1.0, seed=common["seed"])
+    ew = dict(common, potential=rbl.RBL_POT_LJ_EWALD, alpha=EWALD_ALPHA)
+    out = {"workload": "charged LJ fluid: headline positions + neutral random +-1 charges", "alpha": EWALD_ALPHA}
+    for name, kw in (("rbl", {}), ("full_list", {"full_list": True})):
+        s = rbl.System(x, v, L, charges=q, **dict(ew, **kw))
+        s.step(a.warmup)
+        s.autotune(trials=3)
+        ms, (pm, n) = timed(s, a.steps, phases=True)
+        out[name] = {"value": N * a.steps * world / (ms * 1e-3), "ms_per_step": ms / a.steps,
+                     "force_kernel_ms": pm[2] / n, "rebuild_chain_ms": pm[1] / n}
+        del s
+        torch.cuda.empty_cache()
+    out["speedup_vs_full_list"] = out["rbl"]["value"] / out["full_list"]["value"]
+    return out
+
+
 def make_workload(N, seed):
     from paper_2105_04884_gb300 import inputs
 
@@ -590,6 +622,15 @@ def run_ours(a, rank, world, local):
 
     common = dict(r_c=w["rc"], r_s=w["rs"], skin=w["skin"], p=w["p"], dt=w["dt"], T=w["T"], gamma=w["gamma"],
                   seed=1 + rank, cells_per_cutoff=w["K"], precision=rbl.RBL_FP32)
+    ewald = a.potential == "ewald"
+    wname, kname, qself = w["name"], FORCE_KERNEL, 0
+    if ewald:  # the charged fluid is the timed workload (every block below runs it)
+        from paper_2105_04884_gb300 import inputs
+
+        common.update(potential=rbl.RBL_POT_LJ_EWALD, alpha=EWALD_ALPHA,
+                      charges=inputs.charges(N, 1.0, seed=1 + rank))
+        wname = "charged_" + w["name"] + "_ewald_alpha%g" % EWALD_ALPHA
+        kname, qself = FORCE_KERNEL_EWALD, 4
     s = rbl.System(x, v, L, **common)
     s.step(a.warmup)
     tuned = s.autotune(trials=3)  # launch shapes only: no result depends on them
@@ -612,16 +653,16 @@ def run_ours(a, rank, world, local):
     import math as _m
     S = 25 if w["K"] == 2 else (2 * w["K"] + 1) ** 2
     ncell = int(_m.floor(L[0] * w["K"] / (w["rs"] + w["skin"]))) ** 3
-    alg_bytes_pp = 16 + 12 + 4 * nc + 4 * _m.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24
+    alg_bytes_pp = 16 + 12 + 4 * nc + 4 * _m.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24 + qself
     t_force = phase_ms[2] / nsteps * 1e-3
     achieved = alg_bytes_pp * N / t_force / 1e9
     peak, peak_kind = load_peaks()
-    traffic = load_traffic(N)
+    traffic = None if ewald else load_traffic(N)
     result = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded FCC start + Maxwell-Boltzmann velocities)",
-        "config": {"workload": w["name"], "N": N, "rho": w["rho"], "T": w["T"], "r_c": w["rc"], "r_s": w["rs"],
+        "config": {"workload": wname, "N": N, "rho": w["rho"], "T": w["T"], "r_c": w["rc"], "r_s": w["rs"],
                    "skin": w["skin"], "p": p, "dt": w["dt"], "gamma": w["gamma"], "cells_per_cutoff": w["K"],
                    "pair_math": "fp32 + int64 fixed-point sums", "integration": "fp64 BAOAB",
                    "parallelism": "replicas" if world > 1 else "single",
@@ -635,7 +676,7 @@ def run_ours(a, rank, world, local):
         "graph_replay_ms_per_step": ms_graph / a.steps,
         "rebuilds_in_timed_region": obs["n_rebuild"] - obs0["n_rebuild"],
         "rows": {"core_mean": nc, "shell_mean": obs["Ns_mean"], "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"]},
-        "roofline": {"kernel": FORCE_KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes_per_particle": alg_bytes_pp,
                      "traffic": traffic, "traffic_per": "launch"},
@@ -715,6 +756,8 @@ def run_ours(a, rank, world, local):
                          "d2h_bytes_per_step": 48 * N / a.steps + 256,
                          "path": "rbl_set_state(host) + steps x (rbl_step(1) + rbl_observables) + rbl_get_state(host)"}
         del se
+    if not a.no_ewald and not ewald:
+        result["ewald"] = ewald_bench(a, world, x, v, L, common, timed)
     if not a.no_ensemble:
         result["ensemble"] = ensemble_bench(a, rank, timed)
     if not a.no_slab:
@@ -728,7 +771,8 @@ def run_ours(a, rank, world, local):
         mp4, _ = matched_physics_pair(2.0, 10, full=full_run, sampling=1)
         result["matched_physics"] = [mp, mp2, mp3, mp4]
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(x, v, L, a.cpu_steps)
+        result["cpu_baseline"] = cpu_baseline(x, v, L, a.cpu_steps, q=common.get("charges"),
+                                              alpha=common.get("alpha", 0.0))
     if world > 1:
         import torch.distributed as dist
 
@@ -736,10 +780,10 @@ def run_ours(a, rank, world, local):
     return result
 
 
-def cpu_baseline(x, v, L, steps, steps_single=3):
+def cpu_baseline(x, v, L, steps, steps_single=3, q=None, alpha=0.0):
     """The oracle timed on the host cores: OpenMP over every core, and single-threaded
     (the paper's own setting, one core).  Each sample starts from the workload's
-    initial state, so it includes one list build."""
+    initial state, so it includes one list build.  q: charges of the charged fluid."""
     import oracle
 
     w = WORKLOAD
@@ -747,11 +791,11 @@ def cpu_baseline(x, v, L, steps, steps_single=3):
     args = (L, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], w["T"], w["gamma"], 1)
     oracle.set_threads(cores)
     t0 = time.perf_counter()
-    oracle.run(x, v, *args, steps)
+    oracle.run(x, v, *args, steps, q=q, alpha=alpha)
     t = time.perf_counter() - t0
     oracle.set_threads(1)
     t1 = time.perf_counter()
-    oracle.run(x, v, *args, steps_single)
+    oracle.run(x, v, *args, steps_single, q=q, alpha=alpha)
     t1 = time.perf_counter() - t1
     oracle.set_threads(cores)
     return {"value": len(x) * steps / t, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",

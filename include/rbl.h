@@ -7,10 +7,14 @@
  * (r < r_c) summed directly (Eq. (3)) and a shell list (r_c <= r < r_s) from which a
  * random batch of p neighbours is drawn and scaled by N_s/p (Eq. (4)); the mean
  * force is subtracted (Appendix A, F_cor) and the Langevin equation (Eq. (2)) is
- * advanced with a velocity-Verlet splitting (Algorithm 1; Sec. 3).
+ * advanced with a velocity-Verlet splitting (Algorithm 1; Sec. 3).  The pair kernel
+ * is LJ 12-6 (Eq. (1)), optionally plus the Ewald real-space Coulomb term, the
+ * extension the paper names for other short-range kernels (Sec. 2, closing
+ * remarks; Sec. 4).
  *
  * Conventions shared by every entry point
- *  - Units: reduced LJ units, sigma = epsilon = m = k_B = 1.
+ *  - Units: reduced LJ units, sigma = epsilon = m = k_B = 1; charges such that two
+ *    unit charges at distance r have Coulomb energy 1/r.
  *  - Particle arrays passed in or out are in TAG order (row t describes the particle
  *    whose tag is t), AoS [N][3] doubles for positions/velocities/forces.  Inside the
  *    context particles are kept in cell order; the library translates.
@@ -76,6 +80,17 @@ enum { RBL_FP64 = 0, RBL_FP32 = 1 };
  *                     full_list = 0; cells_per_cutoff is not used. */
 enum { RBL_SAMPLE_SHELL = 0, RBL_SAMPLE_STENCIL = 1 };
 
+/* Pair potential of every pair with r < r_s (the RBL applies to any short-range
+ * kernel, Sec. 2 closing remarks and Sec. 4, which name the Ewald real-space term):
+ *  RBL_POT_LJ        (default) u(r) = 4 (r^-12 - r^-6)
+ *  RBL_POT_LJ_EWALD  u(r) = 4 (r^-12 - r^-6) + q_i q_j erfc(alpha r) / r, the short-
+ *                    range part of the Coulomb interaction in an Ewald splitting;
+ *                    r . f adds q_i q_j (erfc(alpha r) / r + 2 alpha / sqrt(pi)
+ *                    exp(-alpha^2 r^2)).  Charges come from rbl_set_charges (all
+ *                    zero until then).  The reciprocal-space and self terms of the
+ *                    Ewald sum are not part of this library. */
+enum { RBL_POT_LJ = 0, RBL_POT_LJ_EWALD = 1 };
+
 typedef struct {
     double L[3];          /* periodic box lengths; each >= 2 (r_s + skin) */
     double r_c;           /* core radius: pairs r < r_c summed directly (Eq. (3)) */
@@ -99,6 +114,8 @@ typedef struct {
                              region's density for inhomogeneous systems (a liquid
                              slab in vapour), else rows overflow (RBL_EOVERFLOW). */
     int sampling;         /* RBL_SAMPLE_SHELL (default) or RBL_SAMPLE_STENCIL */
+    int potential;        /* RBL_POT_LJ (default) or RBL_POT_LJ_EWALD */
+    double alpha;         /* Ewald splitting parameter (> 0) for RBL_POT_LJ_EWALD */
 } rbl_params;
 
 typedef struct {
@@ -107,8 +124,8 @@ typedef struct {
     double K;             /* kinetic energy sum v^2 / 2 */
     double T_kin;         /* 2K / (3N) */
     double P;             /* rho T_kin + W_est / (3V) (no tail) */
-    double U_tail;        /* per-particle tail energy (8/3) pi rho (r_s^-9/3 - r_s^-3) */
-    double P_tail;        /* tail pressure (16/3) pi rho^2 (2 r_s^-9/3 - r_s^-3) */
+    double U_tail;        /* per-particle LJ tail energy (8/3) pi rho (r_s^-9/3 - r_s^-3) */
+    double P_tail;        /* LJ tail pressure (16/3) pi rho^2 (2 r_s^-9/3 - r_s^-3) */
     double net_momentum[3];
     long long step;       /* step counter */
     long long n_rebuild;  /* list builds so far */
@@ -129,7 +146,8 @@ rbl_status rbl_workspace_size(const rbl_params *prm, int N, size_t *bytes);
 
 /* Creates a context (host memory for the handle only).  Validates: N >= 2,
  * 0 < r_c < r_s, skin >= 0, 1 <= p <= 128, dt > 0, T >= 0, gamma >= 0, finite values,
- * every L_a >= 2 (r_s + skin), K in 1..3.  stream is a cudaStream_t (or NULL).
+ * every L_a >= 2 (r_s + skin), K in 1..3, potential RBL_POT_LJ or RBL_POT_LJ_EWALD
+ * (then alpha > 0 and finite).  stream is a cudaStream_t (or NULL).
  * The initial state is zero; load one with rbl_set_state. */
 rbl_status rbl_create(const rbl_params *prm, int N, void *workspace, size_t workspace_bytes, void *stream,
                       rbl_ctx **out);
@@ -154,6 +172,12 @@ int rbl_replicas(const rbl_ctx *ctx);
 /* Loads positions x[N][3] (wrapped into [0, L)), velocities v[N][3] (may be NULL:
  * zero) and the step counter; marks the lists stale.  Rejects non-finite input. */
 rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long long step, int ptr_is_device);
+
+/* Charges q[N] in tag order (packed over replicas) for RBL_POT_LJ_EWALD; they stay
+ * with their particles through every rebuild and rbl_set_state.  Marks the force
+ * stale.  RBL_EINVAL on a context without charges (RBL_POT_LJ) or for a non-finite
+ * charge (checked on the host copy, so host pointers only). */
+rbl_status rbl_set_charges(rbl_ctx *ctx, const double *q);
 
 /* Copies positions and velocities (either may be NULL) out in tag order, and the
  * step counter (may be NULL). */
@@ -262,7 +286,7 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int res
  * first call before any stream capture.  Systems whose workspace (as
  * rbl_workspace_size reports) exceeds 48 MiB are rejected with RBL_ENOMEM (about
  * 60,000 particles at rho* = 0.8 with the default radii); invalid parameters with
- * RBL_EINVAL.  Every call shares the array, so calls that overlap on the GPU (two
+ * RBL_EINVAL, and so is RBL_POT_LJ_EWALD (this call takes no charges).  Every call shares the array, so calls that overlap on the GPU (two
  * streams, two host threads) race: serialise them.  Each call resets the parts it
  * reads; the array keeps the last call's contents otherwise. */
 rbl_status rbl_forces_static(const rbl_params *prm, int N, const double *x, long long step, double *F, void *stream);

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbl.so")
-SOURCES = ["rbl_build.cu", "rbl_force.cu", "rbl_step.cu", "rbl_capi.cu"]
+SOURCES = ["rbl_build.cu", "rbl_force.cu", "rbl_force_ewald.cu", "rbl_step.cu", "rbl_capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-Xcompiler", "-fPIC,-ffp-contract=off"]
 

@@ -256,10 +256,16 @@ __global__ void k_copy_back(View v, int conditional)
         v.x[a * N + k] = v.x_alt[a * N + k];
         v.v[a * N + k] = v.v_alt[a * N + k];
     }
-    v.tag[k] = v.tag_alt[k];
+    const int t = v.tag_alt[k];
+    v.tag[k] = t;
     int4 p = v.pos_alt[k];
     v.pos[k] = p;
     v.ubuild[k] = p;
+    if (v.q) { // charges follow their particles
+        const double qk = v.q_in[v.box[r].first + t];
+        v.q[k] = qk;
+        v.q32[k] = __double2float_rn(qk);
+    }
 }
 
 // K3: two-level lists (or the full list).  One warp per home cell: the warp walks

@@ -66,7 +66,8 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
 {
     if (!p) BAD("params is NULL");
     if (N < 2) BAD("N must be >= 2 (got %d)", N);
-    const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma, p->rho_cap};
+    const double vals[] = {p->L[0], p->L[1], p->L[2], p->r_c, p->r_s, p->skin, p->dt, p->T, p->gamma, p->rho_cap,
+                           p->alpha};
     for (double v : vals)
         if (!std::isfinite(v)) BAD("non-finite parameter");
     if (!(p->r_c > 0.0 && p->r_c < p->r_s)) BAD("need 0 < r_c < r_s (got r_c=%g, r_s=%g)", p->r_c, p->r_s);
@@ -82,6 +83,9 @@ rbl_status validate(const rbl_params *p, int N, char *err, size_t errlen)
     if (p->cap_core < 0 || p->cap_stencil < 0 || !(p->rho_cap >= 0.0)) BAD("capacities must be >= 0");
     if (p->sampling != RBL_SAMPLE_SHELL && p->sampling != RBL_SAMPLE_STENCIL)
         BAD("sampling must be RBL_SAMPLE_SHELL or RBL_SAMPLE_STENCIL");
+    if (p->potential != RBL_POT_LJ && p->potential != RBL_POT_LJ_EWALD)
+        BAD("potential must be RBL_POT_LJ or RBL_POT_LJ_EWALD");
+    if (p->potential == RBL_POT_LJ_EWALD && !(p->alpha > 0.0)) BAD("RBL_POT_LJ_EWALD needs alpha > 0");
     if (p->sampling == RBL_SAMPLE_STENCIL) {
         if (p->full_list) BAD("stencil-pool sampling is an RBL mode: full_list must be 0");
         if (2 * ((int)std::floor(p->r_s / p->r_c) + 1) + 1 > kMaxStencil)
@@ -106,7 +110,7 @@ rbl_status validate_batch(const rbl_params *prm, int R, const int *N, char *err,
             a.gamma != b.gamma || a.precision != b.precision || a.full_list != b.full_list ||
             a.subtract_net_force != b.subtract_net_force || a.cells_per_cutoff != b.cells_per_cutoff ||
             a.cap_core != b.cap_core || a.cap_stencil != b.cap_stencil || a.rho_cap != b.rho_cap ||
-            a.sampling != b.sampling)
+            a.sampling != b.sampling || a.potential != b.potential || a.alpha != b.alpha)
             BAD("replica %d differs from replica 0 in a shared parameter (only L, T, seed may differ)", r);
         slots += round_up_ll(N[r], kTile);
     }
@@ -169,6 +173,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
     P.n_scan_blocks = (P.ncell + 2047) / 2048;
     const size_t Nz = (size_t)P.N;
+    const size_t Nq = p->potential == RBL_POT_LJ_EWALD ? Nz : 0; // charges only with the Ewald term
     size_t st = 48 * (size_t)n_real;                   // packed x and v (host copies)
     if (st < 4 * Nz * (size_t)(p->p + 1)) st = 4 * Nz * (size_t)(p->p + 1); // batch hook
     if (st < (size_t)P.ntile * 32) st = (size_t)P.ntile * 32;               // kinetic partials
@@ -193,6 +198,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
         sizeof(RepScalars) * (size_t)R,             // rs
         sizeof(DevScalars),                         // sc
         P.staging_bytes,                            // staging
+        8 * Nq, 4 * Nq, 8 * Nq,                     // q, q32, q_in
     };
     P.n = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t o = 0;
@@ -249,6 +255,11 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.precision = prm->precision;
     v.subtract = prm->subtract_net_force ? 1 : 0;
     v.sampling = prm->sampling;
+    v.potential = prm->potential;
+    v.alpha = prm->alpha;
+    v.ka = 2.0 * prm->alpha / std::sqrt(kPi);
+    v.alpha32 = (float)v.alpha;
+    v.ka32 = (float)v.ka;
     v.force_threads = 128;
     v.build_warps = 4;
     v.ncell = P.ncell;
@@ -293,6 +304,11 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.rs = (RepScalars *)(base + P.off[k++]);
     v.sc = (DevScalars *)(base + P.off[k++]);
     v.staging = (double *)(base + P.off[k++]);
+    if (prm->potential == RBL_POT_LJ_EWALD) {
+        v.q = (double *)(base + P.off[k++]);
+        v.q32 = (float *)(base + P.off[k++]);
+        v.q_in = (double *)(base + P.off[k++]);
+    }
 }
 
 #define CK(call)                                                                         \
@@ -513,6 +529,11 @@ rbl_status create_impl(const rbl_params *prm, int R, const int *Ns, void *worksp
     if (e == cudaSuccess) e = cudaMemsetAsync(v.rs, 0, sizeof(RepScalars) * (size_t)R, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)P.N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * ((size_t)P.N / kMinBlock), s);
+    if (e == cudaSuccess && v.q) {
+        e = cudaMemsetAsync(v.q, 0, 8 * (size_t)P.N, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(v.q32, 0, 4 * (size_t)P.N, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(v.q_in, 0, 8 * (size_t)P.N, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_err(ctx, "initialisation failed: %s", cudaGetErrorString(e));
@@ -594,6 +615,27 @@ rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long lo
         rbl_status st = check_flags(ctx);
         if (st != RBL_OK) return st;
     }
+    return RBL_OK;
+}
+
+rbl_status rbl_set_charges(rbl_ctx *ctx, const double *q)
+{
+    if (!ctx || !q) return RBL_EINVAL;
+    if (!ctx->view.q) {
+        set_err(ctx, "rbl_set_charges needs potential RBL_POT_LJ_EWALD");
+        return RBL_EINVAL;
+    }
+    for (long long k = 0; k < ctx->n_real; ++k)
+        if (!std::isfinite(q[k])) {
+            set_err(ctx, "charge %lld is not finite", k);
+            return RBL_EINVAL;
+        }
+    double *sq = ctx->view.staging;
+    CK(cudaMemcpyAsync(sq, q, 8 * (size_t)ctx->n_real, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_set_charges(ctx->view, sq, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->force_valid = 0;
+    ctx->energy_valid = 0;
     return RBL_OK;
 }
 
@@ -1133,6 +1175,7 @@ extern "C" rbl_status rbl_forces_static(const rbl_params *prm, int N, const doub
     if (!x || !F || step < 0) return RBL_EINVAL;
     rbl_status st = validate_batch(prm, 1, &N, nullptr, 0);
     if (st != RBL_OK) return st;
+    if (prm->potential != RBL_POT_LJ) return RBL_EINVAL; // no charges can be passed here
     const Plan P = make_plan(prm, 1, &N);
     if (P.total > kStaticScratchBytes) return RBL_ENOMEM;
     void *base = nullptr;

@@ -97,6 +97,9 @@ struct View {
     int ntile;                      // N / kTile
     int p, K, cap_c, W, S, Mcap, full_list, precision, subtract;
     int sampling;                   // RBL_SAMPLE_SHELL or RBL_SAMPLE_STENCIL
+    int potential;                  // RBL_POT_LJ or RBL_POT_LJ_EWALD
+    float alpha32, ka32;            // Ewald alpha and 2 alpha / sqrt(pi), binary32
+    double alpha, ka;               // the same in FP64
     int force_threads;              // threads per block of the force kernel (64, 128 or 256)
     int build_warps;                // home cells (warps) per block of the list build (2, 4 or 8)
     int ncell;                      // cells of all replicas, pad cells included
@@ -111,6 +114,9 @@ struct View {
     int *tag, *tag_alt;             // tag = particle number within its replica
     int4 *pos, *pos_alt;            // (ux, uy, uz, tag) 32-bit fixed-point image
     int4 *ubuild;                   // image at the last build
+    double *q;                      // charges in cell order (RBL_POT_LJ_EWALD; else null)
+    float *q32;                     // the same in binary32 (FP32 pair arithmetic)
+    double *q_in;                   // charges in load order: slot first + t holds tag t's
     void *F;                        // [3][N]: int64 fixed point (FP32 path) or double
     int *cell, *order;
     int *counts, *start, *fill, *blocksums;
@@ -403,6 +409,26 @@ __device__ __forceinline__ float lj_coef(float r2, float *u, float *w)
     return __fmul_rn(vir, inv);
 }
 
+// LJ plus the Ewald real-space term in binary32: u = 4 (r^-12 - r^-6) + qq erfc(alpha
+// r) / r and r . f = 24 (2 r^-12 - r^-6) + qq (erfc(alpha r) / r + ka exp(-alpha^2
+// r^2)), ka = 2 alpha / sqrt(pi); returns the force coefficient (r . f) / r^2.  The
+// LJ terms are formed exactly as in lj_coef; erfcf and expf are CUDA's functions.
+__device__ __forceinline__ float lj_ewald_coef(float r2, float qq, float alpha, float ka, float *u, float *w)
+{
+    float inv = rcp_approx(r2);
+    float r6 = __fmul_rn(__fmul_rn(inv, inv), inv);
+    float t = __fmaf_rn(2.0f, r6, -1.0f);
+    float vlj = __fmul_rn(__fmul_rn(24.0f, r6), t);
+    const float r = __fsqrt_rn(r2);
+    const float ar = __fmul_rn(alpha, r);
+    const float ec = __fmul_rn(erfcf(ar), __frcp_rn(r)); // erfc(alpha r) / r
+    const float ex = expf(-__fmul_rn(ar, ar));           // exp(-alpha^2 r^2)
+    const float vir = __fadd_rn(vlj, __fmul_rn(qq, __fmaf_rn(ka, ex, ec)));
+    if (u) *u = __fadd_rn(__fmul_rn(__fmul_rn(4.0f, r6), __fadd_rn(r6, -1.0f)), __fmul_rn(qq, ec));
+    if (w) *w = vir;
+    return __fmul_rn(vir, inv);
+}
+
 // ---------------------------------------------------------------------------
 // Exact fixed-point accumulation of binary32 values at scale 2^24.  Each value f
 // with |f| < 2^20 is split without rounding error into A = rint(4f) and
@@ -561,5 +587,9 @@ cudaError_t launch_kinetic(const View &v, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);
+cudaError_t launch_set_charges(const View &v, const double *q_packed, cudaStream_t s);
+// The force kernel with the LJ + Ewald real-space pair (its own translation unit).
+cudaError_t launch_force_kernel_ewald(const View &v, int step_offset, bool energy, cudaStream_t s);
+cudaError_t launch_exact_energy_kernel_ewald(const View &v, cudaStream_t s);
 constexpr int kMaxProfileBins = 12288; // shared-memory histogram of one block
 } // namespace rbl

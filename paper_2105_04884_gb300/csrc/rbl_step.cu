@@ -31,6 +31,10 @@ __global__ void k_load(View v, const double *x, const double *vel)
         for (int a = 0; a < 3; ++a) v.x[a * N + i] = v.v[a * N + i] = 0.0;
         v.tag[i] = 0;
         v.pos[i] = v.ubuild[i] = make_int4(0, 0, 0, 0);
+        if (v.q) {
+            v.q[i] = 0.0;
+            v.q32[i] = 0.f;
+        }
         return;
     }
     const Box &b = v.box[r];
@@ -54,7 +58,31 @@ __global__ void k_load(View v, const double *x, const double *vel)
     v.tag[i] = t;
     v.pos[i] = make_int4((int)u[0], (int)u[1], (int)u[2], t);
     v.ubuild[i] = v.pos[i];
+    if (v.q) {
+        v.q[i] = v.q_in[i];
+        v.q32[i] = __double2float_rn(v.q_in[i]);
+    }
     if (bad) atomicOr(&v.sc->flags, kFlagNonFinite);
+}
+
+// Charges from packed tag-ordered input: into load order (slot first + t for tag
+// t, zero on padding slots) and, through each slot's tag, into the current order.
+__global__ void k_set_charges(View v, const double *q)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) {
+        v.q_in[i] = v.q[i] = 0.0;
+        v.q32[i] = 0.f;
+        return;
+    }
+    const Box &b = v.box[r];
+    v.q_in[i] = q[(size_t)b.in0 + (size_t)(i - b.first)];
+    const double qi = q[(size_t)b.in0 + (size_t)v.tag[i]];
+    v.q[i] = qi;
+    v.q32[i] = __double2float_rn(qi);
 }
 
 // SoA cell-ordered state -> packed AoS tag-ordered output.
@@ -271,6 +299,12 @@ cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s)
 cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s)
 {
     k_load<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_charges(const View &v, const double *q_packed, cudaStream_t s)
+{
+    k_set_charges<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, q_packed);
     return cudaGetLastError();
 }
 

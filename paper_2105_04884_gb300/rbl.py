@@ -9,6 +9,9 @@ is no fallback path.
 
     ens = Ensemble([Replica(x0, v0, L0, T0, seed0), ...], r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005)
     ens.step(100); obs = ens.observables()  # one dict per replica
+
+    # LJ plus the Ewald real-space term q_i q_j erfc(alpha r) / r
+    sys = System(x, v, L, 1.5, 3.5, 0.3, 10, 0.005, potential=RBL_POT_LJ_EWALD, alpha=1.0, charges=q)
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ from . import _build
 
 RBL_FP64, RBL_FP32 = 0, 1
 RBL_SAMPLE_SHELL, RBL_SAMPLE_STENCIL = 0, 1
+RBL_POT_LJ, RBL_POT_LJ_EWALD = 0, 1
 STATUS = {0: "RBL_OK", 1: "RBL_EINVAL", 2: "RBL_ENOMEM", 3: "RBL_EOVERFLOW", 4: "RBL_ENONFINITE",
           5: "RBL_ETIMEOUT", 6: "RBL_ECUDA"}
 
@@ -37,7 +41,8 @@ class rbl_params(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int),
                 ("full_list", ctypes.c_int), ("subtract_net_force", ctypes.c_int),
                 ("cells_per_cutoff", ctypes.c_int), ("cap_core", ctypes.c_int), ("cap_stencil", ctypes.c_int),
-                ("rho_cap", ctypes.c_double), ("sampling", ctypes.c_int)]
+                ("rho_cap", ctypes.c_double), ("sampling", ctypes.c_int), ("potential", ctypes.c_int),
+                ("alpha", ctypes.c_double)]
 
 
 class rbl_obs(ctypes.Structure):
@@ -55,7 +60,7 @@ class rbl_obs(ctypes.Structure):
 
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
-           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_get_state", "rbl_build_lists",
+           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_set_charges", "rbl_get_state", "rbl_build_lists",
            "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
            "rbl_get_batch", "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config",
            "rbl_autotune", "rbl_set_phase_timing", "rbl_phase_times",
@@ -88,6 +93,7 @@ def load(build_if_missing: bool = False):
     L.rbl_create_batch.argtypes = [ctypes.POINTER(rbl_params), I, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
     L.rbl_replicas.argtypes = [P]
     L.rbl_set_state.argtypes = [P, P, P, LL, I]
+    L.rbl_set_charges.argtypes = [P, P]
     L.rbl_get_state.argtypes = [P, P, P, ctypes.POINTER(LL), I]
     L.rbl_build_lists.argtypes = [P]
     L.rbl_forces.argtypes = [P, P, I]
@@ -119,7 +125,7 @@ def load(build_if_missing: bool = False):
 
 def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32, full_list=False,
                 subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, rho_cap=0.0,
-                sampling=RBL_SAMPLE_SHELL) -> rbl_params:
+                sampling=RBL_SAMPLE_SHELL, potential=RBL_POT_LJ, alpha=0.0) -> rbl_params:
     prm = rbl_params()
     load().rbl_params_default(ctypes.byref(prm))
     Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
@@ -134,6 +140,8 @@ def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RB
     prm.cap_core, prm.cap_stencil = int(cap_core), int(cap_stencil)
     prm.rho_cap = float(rho_cap)
     prm.sampling = int(sampling)
+    prm.potential = int(potential)
+    prm.alpha = float(alpha)
     return prm
 
 
@@ -209,6 +217,13 @@ class _Context:
             x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
             v = None if v is None else np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         self._check(self.lib.rbl_set_state(self.h, _ptr(x), _ptr(v), int(step), int(dev)))
+
+    def set_charges(self, q):
+        """Charges in tag order (packed over replicas), host array."""
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+        if q.shape[0] != self.N:
+            raise ValueError(f"need {self.N} charges (got {q.shape[0]})")
+        self._check(self.lib.rbl_set_charges(self.h, _ptr(q)))
 
     def get_state(self, device=False):
         if device:
@@ -309,12 +324,15 @@ class System(_Context):
 
     def __init__(self, x, v, L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RBL_FP32,
                  full_list=False, subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0,
-                 stream=None, device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL):
+                 stream=None, device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL, potential=RBL_POT_LJ,
+                 alpha=0.0, charges=None):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) if not hasattr(x, "data_ptr") else x
         prm = make_params(L, r_c, r_s, skin, p, dt, T, gamma, seed, precision, full_list, subtract_net_force,
-                          cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling)
+                          cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling, potential, alpha)
         self._create([prm], [int(x.shape[0])], stream, device)
         self.set_state(x, v, step)
+        if charges is not None:
+            self.set_charges(charges)
 
     def observables(self) -> dict:
         return self._observables()[0]
@@ -339,10 +357,11 @@ class System(_Context):
 class Replica:
     """One member of an ensemble: its state, box, bath temperature and seed."""
 
-    def __init__(self, x, v, L, T, seed):
+    def __init__(self, x, v, L, T, seed, q=None):
         self.x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
         self.v = None if v is None else np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         self.L, self.T, self.seed = L, T, seed
+        self.q = None if q is None else np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
 
 
 class Ensemble(_Context):
@@ -351,15 +370,20 @@ class Ensemble(_Context):
 
     def __init__(self, replicas, r_c, r_s, skin, p, dt, gamma=0.0, precision=RBL_FP32, full_list=False,
                  subtract_net_force=True, cells_per_cutoff=2, cap_core=0, cap_stencil=0, step=0, stream=None,
-                 device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL):
+                 device=None, rho_cap=0.0, sampling=RBL_SAMPLE_SHELL, potential=RBL_POT_LJ, alpha=0.0):
         prms = [make_params(rp.L, r_c, r_s, skin, p, dt, rp.T, gamma, rp.seed, precision, full_list,
-                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling)
+                            subtract_net_force, cells_per_cutoff, cap_core, cap_stencil, rho_cap, sampling,
+                            potential, alpha)
                 for rp in replicas]
         self._create(prms, [len(rp.x) for rp in replicas], stream, device)
         self.offsets = np.concatenate([[0], np.cumsum(self.Ns)])
         x = np.concatenate([rp.x for rp in replicas])
         v = np.concatenate([rp.v if rp.v is not None else np.zeros_like(rp.x) for rp in replicas])
         self.set_state(x, v, step)
+        if potential == RBL_POT_LJ_EWALD:  # replicas without charges (q None) get zeros
+            q = [getattr(rp, "q", None) for rp in replicas]
+            self.set_charges(np.concatenate([qr if qr is not None else np.zeros(len(rp.x))
+                                             for qr, rp in zip(q, replicas)]))
 
     def split(self, a):
         """Packed per-particle rows -> list of per-replica arrays."""

@@ -62,6 +62,9 @@ def test_workspace_size_and_validation(lib):
         dict(L=[7.0, 10.772, 10.772]),          # box below 2 (r_s + skin)
         dict(cells_per_cutoff=4),
         dict(T=float("nan")),
+        dict(potential=2),                      # unknown pair potential
+        dict(potential=1, alpha=0.0),           # Ewald term without a splitting parameter
+        dict(potential=1, alpha=float("inf")),
     ]
     for kw in bad:
         args = dict(L=[10.772] * 3, r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005)
@@ -69,6 +72,10 @@ def test_workspace_size_and_validation(lib):
         prm = rbl.make_params(**args)
         assert _size(prm, 1000)[0] == 1, kw
     assert _size(rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005), 1)[0] == 1  # N < 2
+    # the Ewald term adds the charge arrays to the workspace
+    st, ne = _size(rbl.make_params([10.772] * 3, 1.5, 3.5, 0.3, 10, 0.005, potential=rbl.RBL_POT_LJ_EWALD,
+                                   alpha=1.0), 1000)
+    assert st == 0 and ne > n1
 
 
 def test_create_rejects_bad_workspace(lib):
