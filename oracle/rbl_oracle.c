@@ -363,8 +363,8 @@ void orc_cells(int n, const uint32_t *u, const double L[3], double rs, double sk
 
 /* ------------------------------------------------------------------------- */
 /* Two-level neighbour lists with a skin (Sec. 2: core list from the nearest
- * cells, shell list from the stencil; the cell edge "slightly larger" than the
- * cutoff so lists survive several steps):
+ * cells, shell list from the stencil; the cell edge a little larger than the
+ * cutoff so that lists survive several steps):
  *   core_i  = { j != i : r2 <  (r_c + skin)^2 }
  *   shell_i = { j != i : max(r_c - skin, 0)^2 <= r2 < (r_s + skin)^2 }
  *   full_i  = { j != i : r2 <  (r_s + skin)^2 }      (classical Verlet list)

@@ -412,10 +412,21 @@ rbl_status ensure_events(rbl_ctx *ctx, int steps)
 // device rebuild flag into a conditional handle, an IF node whose body is the whole
 // rebuild chain, then the force and its reduction.  No host round trip and no
 // empty launches when no rebuild is due.
-rbl_status ensure_graph(rbl_ctx *ctx)
+// The captured steps.  Every step is kick(ck) + drift (+ O), the device-conditional
+// rebuild chain, the force at n + 1 and its reduction; the first step of a call
+// opens with a half kick, and the last one (energy estimates refreshed) ends with
+// the closing half kick, so a call of n >= 2 steps replays FIRST, MID^(n-2), LAST
+// and a call of one step SINGLE.
+enum StepGraph { kGraphMid = 0, kGraphFirst = 1, kGraphLast = 2, kGraphSingle = 3 };
+
+rbl_status ensure_graph(rbl_ctx *ctx, int kind)
 {
-    if (ctx->graph_exec) return RBL_OK;
+    if (ctx->graph_exec[kind]) return RBL_OK;
+    const bool half = kind == kGraphFirst || kind == kGraphSingle;
+    const bool last = kind == kGraphLast || kind == kGraphSingle;
+    const double ck = half ? 0.5 * ctx->prm.dt : ctx->prm.dt;
     cudaStream_t s = ctx->stream;
+    CK(launch_force_kernel(ctx->view, 1, last, s, true)); // kernel attributes, before the capture
     cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
@@ -425,7 +436,7 @@ rbl_status ensure_graph(rbl_ctx *ctx)
     cudaGraphNodeParams cp = {};
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, mode);
     if (e == cudaSuccess) {
-        cudaError_t ec = launch_integrate(ctx->view, ctx->prm.dt, true, s);
+        cudaError_t ec = launch_integrate(ctx->view, ck, true, s);
         if (ec == cudaSuccess) ec = launch_set_rebuild_condition(ctx->view, handle, s);
         cudaStreamCaptureStatus cst;
         const cudaGraphNode_t *deps = nullptr;
@@ -439,7 +450,8 @@ rbl_status ensure_graph(rbl_ctx *ctx)
             ec = cudaGraphAddNode(&cond_node, g, deps, nullptr, ndeps, &cp);
         }
         if (ec == cudaSuccess) ec = cudaStreamUpdateCaptureDependencies(s, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (ec == cudaSuccess) ec = launch_forces(ctx->view, 1, 1, false, s);
+        if (ec == cudaSuccess) ec = launch_forces(ctx->view, 1, 1, last, s);
+        if (ec == cudaSuccess && last) ec = launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, s);
         cudaGraph_t gout = nullptr;
         e = cudaStreamEndCapture(s, &gout);
         if (ec != cudaSuccess) e = ec;
@@ -464,10 +476,18 @@ rbl_status ensure_graph(rbl_ctx *ctx)
         set_err(ctx, "building the step graph failed: %s", cudaGetErrorString(e));
         return RBL_ECUDA;
     }
-    ctx->graph_exec = ex;
+    ctx->graph_exec[kind] = ex;
     return RBL_OK;
 }
 
+void drop_graphs(rbl_ctx *ctx)
+{
+    for (cudaGraphExec_t &g : ctx->graph_exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
 
 rbl_status create_impl(const rbl_params *prm, int R, const int *Ns, void *workspace, size_t workspace_bytes,
                        void *stream, rbl_ctx **out)
@@ -713,19 +733,22 @@ rbl_status rbl_step(rbl_ctx *ctx, int n)
         ctx->energy_valid = 1;
         return check_flags(ctx);
     }
-    CK(enqueue_step(ctx, 0.5 * ctx->prm.dt, n == 1));
-    if (n > 2) {
-        if (ctx->stream == nullptr) {
-            // the legacy default stream cannot be captured: launch directly
-            for (int k = 1; k < n - 1; ++k) CK(enqueue_step(ctx, ctx->prm.dt, false));
-        } else {
-            st = ensure_graph(ctx);
-            if (st != RBL_OK) return st;
-            for (int k = 1; k < n - 1; ++k) CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
-        }
+    if (ctx->stream == nullptr) {
+        // the legacy default stream cannot be captured: launch directly
+        CK(enqueue_step(ctx, 0.5 * ctx->prm.dt, n == 1));
+        for (int k = 1; k < n - 1; ++k) CK(enqueue_step(ctx, ctx->prm.dt, false));
+        if (n > 1) CK(enqueue_step(ctx, ctx->prm.dt, true));
+        CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+    } else {
+        const int first = n == 1 ? kGraphSingle : kGraphFirst;
+        st = ensure_graph(ctx, first);
+        if (st == RBL_OK && n > 2) st = ensure_graph(ctx, kGraphMid);
+        if (st == RBL_OK && n > 1) st = ensure_graph(ctx, kGraphLast);
+        if (st != RBL_OK) return st;
+        CK(cudaGraphLaunch(ctx->graph_exec[first], ctx->stream));
+        for (int k = 1; k < n - 1; ++k) CK(cudaGraphLaunch(ctx->graph_exec[kGraphMid], ctx->stream));
+        if (n > 1) CK(cudaGraphLaunch(ctx->graph_exec[kGraphLast], ctx->stream));
     }
-    if (n > 1) CK(enqueue_step(ctx, ctx->prm.dt, true));
-    CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
     ctx->step += n;
     ctx->force_valid = 1;
     ctx->energy_valid = 1;
@@ -998,10 +1021,7 @@ rbl_status rbl_set_launch_config(rbl_ctx *ctx, int force_threads, int build_warp
     if (ctx->view.force_threads != force_threads || ctx->view.build_warps != build_warps) {
         ctx->view.force_threads = force_threads;
         ctx->view.build_warps = build_warps;
-        if (ctx->graph_exec) { // the captured step holds the old launch shapes
-            cudaGraphExecDestroy(ctx->graph_exec);
-            ctx->graph_exec = nullptr;
-        }
+        drop_graphs(ctx); // the captured steps hold the old launch shapes
     }
     return RBL_OK;
 }
@@ -1101,7 +1121,7 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int res
 void rbl_destroy(rbl_ctx *ctx)
 {
     if (!ctx) return;
-    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    drop_graphs(ctx);
     for (int k = 0; k < ctx->ev_cap * 5; ++k) cudaEventDestroy(ctx->ev[k]);
     std::free(ctx->ev);
     delete ctx->h_sc;

@@ -184,10 +184,10 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
 
 } // namespace
 
-cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s)
+cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s, bool prepare)
 {
-    if (v.potential == RBL_POT_LJ_EWALD) return launch_force_kernel_ewald(v, step_offset, energy, s);
-    return launch_force_dispatch<false>(v, step_offset, energy, s);
+    if (v.potential == RBL_POT_LJ_EWALD) return launch_force_kernel_ewald(v, step_offset, energy, s, prepare);
+    return launch_force_dispatch<false>(v, step_offset, energy, s, prepare);
 }
 
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s)

@@ -7,9 +7,9 @@
 
 namespace rbl {
 
-cudaError_t launch_force_kernel_ewald(const View &v, int step_offset, bool energy, cudaStream_t s)
+cudaError_t launch_force_kernel_ewald(const View &v, int step_offset, bool energy, cudaStream_t s, bool prepare)
 {
-    return launch_force_dispatch<true>(v, step_offset, energy, s);
+    return launch_force_dispatch<true>(v, step_offset, energy, s, prepare);
 }
 
 cudaError_t launch_exact_energy_kernel_ewald(const View &v, cudaStream_t s)

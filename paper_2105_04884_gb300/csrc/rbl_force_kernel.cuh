@@ -212,7 +212,7 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 #define RBL_FORCE_REGS 72
 #endif
 constexpr int kForceRegs = RBL_FORCE_REGS;
-constexpr int kForceRegsEwald = 96; // erfc and exp need more: 5 blocks of 128 threads per SM
+constexpr int kForceRegsEwald = 80; // the Ewald term needs more: 6 blocks of 128 threads per SM
 static_assert(kMinBlock == 64 && kMaxForceThreads % 64 == 0, "per-block partials are sized for kMinBlock");
 constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
 constexpr int kGather = 8;
@@ -525,15 +525,17 @@ __global__ void __maxnreg__(FP32 ? (EWALD ? kForceRegsEwald : kForceRegs) : 128)
 
 // Launch k_force with the context's block size and its staging in dynamic shared
 // memory (opting in to more than the default 48 KB where the largest block needs it).
+// prepare = true: only set the shared-memory attribute (before a stream capture of
+// this launch), launch nothing.
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>
-cudaError_t launch_k_force(const View &v, int step_offset, cudaStream_t s)
+cudaError_t launch_k_force(const View &v, int step_offset, cudaStream_t s, bool prepare = false)
 {
     const int bd = v.force_threads;
     const size_t smem = (size_t)kMaskStage * bd * (sizeof(unsigned) + sizeof(unsigned short));
     if (smem > 40 * 1024) {
         // beyond the default limit together with the kernel's static shared memory:
-        // a function attribute, set outside stream capture (a step always launches
-        // this kernel directly before its graph is captured)
+        // a function attribute, set outside stream capture (the graphs of a step are
+        // captured after a prepare call)
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaError_t e = cudaStreamIsCapturing(s, &cs);
         if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
@@ -541,29 +543,30 @@ cudaError_t launch_k_force(const View &v, int step_offset, cudaStream_t s)
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    if (prepare) return cudaSuccess;
     k_force<MODE, FP32, ENERGY, PMAX, EWALD><<<ceil_div(v.N, bd), bd, smem, s>>>(v, step_offset);
     return cudaGetLastError();
 }
 
 template <int MODE, bool FP32, bool ENERGY, bool EWALD>
-cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s)
+cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s, bool prepare)
 {
     if constexpr (MODE == 1) {
-        return launch_k_force<MODE, FP32, ENERGY, 0, EWALD>(v, step_offset, s);
+        return launch_k_force<MODE, FP32, ENERGY, 0, EWALD>(v, step_offset, s, prepare);
     } else {
         // every rank slot up to PMAX is resolved, so PMAX is p itself for the usual
         // batch sizes and a bound otherwise
         switch (v.p) {
-        case 1: return launch_k_force<MODE, FP32, ENERGY, 1, EWALD>(v, step_offset, s);
-        case 2: return launch_k_force<MODE, FP32, ENERGY, 2, EWALD>(v, step_offset, s);
-        case 5: return launch_k_force<MODE, FP32, ENERGY, 5, EWALD>(v, step_offset, s);
-        case 10: return launch_k_force<MODE, FP32, ENERGY, 10, EWALD>(v, step_offset, s);
-        case 20: return launch_k_force<MODE, FP32, ENERGY, 20, EWALD>(v, step_offset, s);
+        case 1: return launch_k_force<MODE, FP32, ENERGY, 1, EWALD>(v, step_offset, s, prepare);
+        case 2: return launch_k_force<MODE, FP32, ENERGY, 2, EWALD>(v, step_offset, s, prepare);
+        case 5: return launch_k_force<MODE, FP32, ENERGY, 5, EWALD>(v, step_offset, s, prepare);
+        case 10: return launch_k_force<MODE, FP32, ENERGY, 10, EWALD>(v, step_offset, s, prepare);
+        case 20: return launch_k_force<MODE, FP32, ENERGY, 20, EWALD>(v, step_offset, s, prepare);
         default:
-            if (v.p <= 8) return launch_k_force<MODE, FP32, ENERGY, 8, EWALD>(v, step_offset, s);
-            if (v.p <= 16) return launch_k_force<MODE, FP32, ENERGY, 16, EWALD>(v, step_offset, s);
-            if (v.p <= 32) return launch_k_force<MODE, FP32, ENERGY, 32, EWALD>(v, step_offset, s);
-            return launch_k_force<MODE, FP32, ENERGY, 0, EWALD>(v, step_offset, s);
+            if (v.p <= 8) return launch_k_force<MODE, FP32, ENERGY, 8, EWALD>(v, step_offset, s, prepare);
+            if (v.p <= 16) return launch_k_force<MODE, FP32, ENERGY, 16, EWALD>(v, step_offset, s, prepare);
+            if (v.p <= 32) return launch_k_force<MODE, FP32, ENERGY, 32, EWALD>(v, step_offset, s, prepare);
+            return launch_k_force<MODE, FP32, ENERGY, 0, EWALD>(v, step_offset, s, prepare);
         }
     }
 }
@@ -571,22 +574,22 @@ cudaError_t launch_force_p(const View &v, int step_offset, cudaStream_t s)
 
 // The force kernel for the context's mode, precision and batch size.
 template <bool EWALD>
-cudaError_t launch_force_dispatch(const View &v, int step_offset, bool energy, cudaStream_t s)
+cudaError_t launch_force_dispatch(const View &v, int step_offset, bool energy, cudaStream_t s, bool prepare)
 {
     bool fp32 = v.precision == RBL_FP32;
     if (v.full_list) {
-        if (!fp32) return launch_force_p<1, false, true, EWALD>(v, step_offset, s);
-        return energy ? launch_force_p<1, true, true, EWALD>(v, step_offset, s)
-                      : launch_force_p<1, true, false, EWALD>(v, step_offset, s);
+        if (!fp32) return launch_force_p<1, false, true, EWALD>(v, step_offset, s, prepare);
+        return energy ? launch_force_p<1, true, true, EWALD>(v, step_offset, s, prepare)
+                      : launch_force_p<1, true, false, EWALD>(v, step_offset, s, prepare);
     }
     if (v.sampling) {
-        if (!fp32) return launch_force_p<3, false, true, EWALD>(v, step_offset, s);
-        return energy ? launch_force_p<3, true, true, EWALD>(v, step_offset, s)
-                      : launch_force_p<3, true, false, EWALD>(v, step_offset, s);
+        if (!fp32) return launch_force_p<3, false, true, EWALD>(v, step_offset, s, prepare);
+        return energy ? launch_force_p<3, true, true, EWALD>(v, step_offset, s, prepare)
+                      : launch_force_p<3, true, false, EWALD>(v, step_offset, s, prepare);
     }
-    if (!fp32) return launch_force_p<0, false, true, EWALD>(v, step_offset, s);
-    return energy ? launch_force_p<0, true, true, EWALD>(v, step_offset, s)
-                  : launch_force_p<0, true, false, EWALD>(v, step_offset, s);
+    if (!fp32) return launch_force_p<0, false, true, EWALD>(v, step_offset, s, prepare);
+    return energy ? launch_force_p<0, true, true, EWALD>(v, step_offset, s, prepare)
+                  : launch_force_p<0, true, false, EWALD>(v, step_offset, s, prepare);
 }
 
 // MODE 2 (exact energy and virial) in the context's precision.

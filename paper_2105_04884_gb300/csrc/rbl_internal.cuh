@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "rbl.h"
+#include "rbl_erfc_fit.cuh"
 
 namespace rbl {
 
@@ -409,20 +410,41 @@ __device__ __forceinline__ float lj_coef(float r2, float *u, float *w)
     return __fmul_rn(vir, inv);
 }
 
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // LJ plus the Ewald real-space term in binary32: u = 4 (r^-12 - r^-6) + qq erfc(alpha
 // r) / r and r . f = 24 (2 r^-12 - r^-6) + qq (erfc(alpha r) / r + ka exp(-alpha^2
 // r^2)), ka = 2 alpha / sqrt(pi); returns the force coefficient (r . f) / r^2.  The
-// LJ terms are formed exactly as in lj_coef; erfcf and expf are CUDA's functions.
+// LJ terms are formed exactly as in lj_coef.  erfc(x) = t h(t) exp(-x^2) with
+// t = 1 / (1 + P x) and h the fitted polynomial of rbl_erfc_fit.cuh (relative error
+// about 1e-7), so the one exponential serves both terms; 1/r, the reciprocal and
+// 2^x come from the hardware approximations (within 2 ulp).
 __device__ __forceinline__ float lj_ewald_coef(float r2, float qq, float alpha, float ka, float *u, float *w)
 {
     float inv = rcp_approx(r2);
     float r6 = __fmul_rn(__fmul_rn(inv, inv), inv);
     float t = __fmaf_rn(2.0f, r6, -1.0f);
     float vlj = __fmul_rn(__fmul_rn(24.0f, r6), t);
-    const float r = __fsqrt_rn(r2);
-    const float ar = __fmul_rn(alpha, r);
-    const float ec = __fmul_rn(erfcf(ar), __frcp_rn(r)); // erfc(alpha r) / r
-    const float ex = expf(-__fmul_rn(ar, ar));           // exp(-alpha^2 r^2)
+    const float ir = rsqrt_approx(r2);                           // 1 / r
+    const float ar = __fmul_rn(alpha, __fmul_rn(r2, ir));        // alpha r
+    const float tt = rcp_approx(__fmaf_rn(kErfcP, ar, 1.0f));
+    float hp = erfc_fit_coef(kErfcDegree);
+#pragma unroll
+    for (int k = kErfcDegree - 1; k >= 0; --k) hp = __fmaf_rn(hp, tt, erfc_fit_coef(k));
+    const float ex = ex2_approx(__fmul_rn(__fmul_rn(ar, ar), -1.44269504f)); // exp(-alpha^2 r^2)
+    const float ec = __fmul_rn(__fmul_rn(__fmul_rn(tt, hp), ex), ir);       // erfc(alpha r) / r
     const float vir = __fadd_rn(vlj, __fmul_rn(qq, __fmaf_rn(ka, ex, ec)));
     if (u) *u = __fadd_rn(__fmul_rn(__fmul_rn(4.0f, r6), __fadd_rn(r6, -1.0f)), __fmul_rn(qq, ec));
     if (w) *w = vir;
@@ -556,7 +578,7 @@ struct rbl_ctx {
     int energy_valid;  // energy/virial estimates match F
     long long step;    // host mirror of the step counter
     size_t staging_bytes;
-    cudaGraphExec_t graph_exec; // captured steady-state step
+    cudaGraphExec_t graph_exec[4]; // captured steps: middle, first, last, single (enum StepGraph)
     int phase_timing;           // rbl_set_phase_timing
     cudaEvent_t *ev;            // 5 events per timed step
     int ev_cap;                 // steps the event pool covers
@@ -577,7 +599,8 @@ cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream
 cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s);
 cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
-cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s);
+// prepare = true: set the kernel's attributes for a later captured launch, launch nothing
+cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cudaStream_t s, bool prepare = false);
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s);
 cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s);
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
@@ -589,7 +612,7 @@ cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *h
 cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_set_charges(const View &v, const double *q_packed, cudaStream_t s);
 // The force kernel with the LJ + Ewald real-space pair (its own translation unit).
-cudaError_t launch_force_kernel_ewald(const View &v, int step_offset, bool energy, cudaStream_t s);
+cudaError_t launch_force_kernel_ewald(const View &v, int step_offset, bool energy, cudaStream_t s, bool prepare);
 cudaError_t launch_exact_energy_kernel_ewald(const View &v, cudaStream_t s);
 constexpr int kMaxProfileBins = 12288; // shared-memory histogram of one block
 } // namespace rbl

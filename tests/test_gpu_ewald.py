@@ -4,7 +4,7 @@ closing remarks, Sec. 4) through the C ABI, against the oracle on the same seede
 charged LJ fluid (FCC start, neutral random +-1 charges).
 
 Bars: forces ||F_gpu - F_orc|| / ||F_orc|| <= 1e-12 (FP64 path) and <= 1e-5 (FP32
-path; erfcf and expf are within a few ulp); exact energy 1e-11 (FP64); trajectories
+path: the kernel's own erfc fit is within about 1e-7); exact energy 1e-11 (FP64); trajectories
 as in the LJ dynamics test; ensembles and reloads bit-exact.
 """
 import numpy as np
