@@ -139,7 +139,7 @@ def load_peaks():
 
 def load_traffic(N):
     """DRAM bytes per launch of the force kernel from the committed ncu summary, if it
-    was taken on the current kernel source (else None).  The capture is of a smaller
+    was taken on the current force-kernel and list-build sources (else None).  The capture is of a smaller
     system; traffic grows in proportion to N, so it is scaled per particle."""
     path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
     try:
@@ -147,7 +147,7 @@ def load_traffic(N):
             d = json.load(fh)
         from paper_2105_04884_gb300 import _build
 
-        if d.get("source_sha") != _build.source_digest():
+        if d.get("source_sha") != _build.force_digest():
             return None
         return float(d["dram_bytes_per_particle"]) * N
     except Exception:
@@ -730,8 +730,10 @@ def run_ours(a, rank, world, local):
                                       "speedup_vs_shell_list": v3 / value}
         del s3
         torch.cuda.empty_cache()
-    # end to end through the C ABI with host buffers: upload once, K x (step + scalar
-    # readback), download the final state
+    # end to end through the C ABI with host buffers: upload once, K x (one step + that
+    # step's observables into host memory), download the final state.  e2e: the
+    # observables of every step copied asynchronously into a page-locked ring that the
+    # host reads after the final download; e2e_sync: rbl_observables, which waits, each step.
     if not a.no_e2e:
         import ctypes
 
@@ -743,24 +745,42 @@ def run_ours(a, rank, world, local):
         vh = torch.from_numpy(v).pin_memory()
         xo = torch.empty_like(xh).pin_memory()
         vo = torch.empty_like(vh).pin_memory()
+        osz = ctypes.sizeof(rbl.rbl_obs)
+        ring = torch.empty(a.steps * osz, dtype=torch.uint8).pin_memory()
         obs_c = rbl.rbl_obs()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()), 0, 0))
-        for _ in range(a.steps):
-            se._check(se.lib.rbl_step(se.h, 1))
-            se._check(se.lib.rbl_observables(se.h, ctypes.byref(obs_c)))
-        step = ctypes.c_longlong()
-        se._check(se.lib.rbl_get_state(se.h, ctypes.c_void_p(xo.data_ptr()), ctypes.c_void_p(vo.data_ptr()),
-                                       ctypes.byref(step), 0))
-        torch.cuda.synchronize()
-        te = max_over_ranks(time.perf_counter() - t0)
-        barrier()
+        e2e = {}
+        for mode in ("async", "sync"):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()), 0,
+                                           0))
+            for k in range(a.steps):
+                if mode == "async":
+                    se._check(se.lib.rbl_step_async(se.h, 1))
+                    se._check(se.lib.rbl_observables_async(se.h, ctypes.c_void_p(ring.data_ptr() + k * osz), 0))
+                else:
+                    se._check(se.lib.rbl_step(se.h, 1))
+                    se._check(se.lib.rbl_observables(se.h, ctypes.byref(obs_c)))
+            step = ctypes.c_longlong()
+            se._check(se.lib.rbl_get_state(se.h, ctypes.c_void_p(xo.data_ptr()), ctypes.c_void_p(vo.data_ptr()),
+                                           ctypes.byref(step), 0))
+            if mode == "async":  # the host reads every step's scalars
+                obs_all = (rbl.rbl_obs * a.steps).from_buffer_copy(ring.numpy().tobytes())
+                t_mean = sum(o.T_kin for o in obs_all) / a.steps
+            torch.cuda.synchronize()
+            e2e[mode] = max_over_ranks(time.perf_counter() - t0)
+            barrier()
+        te = e2e["async"]
         result["e2e"] = {"value": N * a.steps * world / te, "unit": "particle-steps/s",
                          "h2d_bytes_per_step": 48 * N / a.steps,
-                         "d2h_bytes_per_step": 48 * N / a.steps + 256,
-                         "path": "rbl_set_state(host) + steps x (rbl_step(1) + rbl_observables) + rbl_get_state(host)"}
+                         "d2h_bytes_per_step": 48 * N / a.steps + osz,
+                         "path": "rbl_set_state(host) + steps x (rbl_step_async(1) + rbl_observables_async into "
+                                 "a page-locked ring) + rbl_get_state(host, waits and reports device flags) + host "
+                                 "read of every step's rbl_obs",
+                         "T_kin_mean": t_mean}
+        result["e2e_sync"] = {"value": N * a.steps * world / e2e["sync"], "unit": "particle-steps/s",
+                              "path": "as e2e with rbl_step(1) and rbl_observables, each of which waits"}
         del se
     if not a.no_ewald and not ewald:
         result["ewald"] = ewald_bench(a, world, x, v, L, common, timed)

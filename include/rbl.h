@@ -201,10 +201,24 @@ rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device);
  * Synchronises at the end and reports device flags. */
 rbl_status rbl_step(rbl_ctx *ctx, int n);
 
+/* rbl_step without the wait: enqueues the n steps on the context's stream and returns.
+ * Device flags are reported by the next call that synchronises.  With phase timing
+ * enabled it is rbl_step. */
+rbl_status rbl_step_async(rbl_ctx *ctx, int n);
+
 /* Scalars of the current state (kinetic terms from the current velocities, energy
  * and virial from the last force evaluation), out[R]: one per replica.
  * Synchronises. */
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
+
+/* rbl_observables without the wait: enqueues on the context's stream the kinetic sums,
+ * the assembly of the same rbl_obs[R] values on the device, and their copy into
+ * out[R] (host memory, page-locked for the copy to be asynchronous, or device memory
+ * with ptr_is_device = 1), and returns.  out is valid once the stream has reached the
+ * copy (synchronise the stream, or make any synchronising call).  Device flags are
+ * not read here; the next synchronising call reports them.  For reading the scalars
+ * every step without stalling the step sequence. */
+rbl_status rbl_observables_async(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device);
 
 /* The energy and virial of the truncated potential at the current positions, with
  * no sampling: *U = sum over pairs i<j with r_ij < r_s of u(r_ij), *W the virial

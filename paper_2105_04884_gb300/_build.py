@@ -31,18 +31,31 @@ def _deps():
     return files
 
 
-def source_digest() -> str:
-    """sha256 of the library sources (identifies the kernels a profile was taken on)."""
+# The sources that fix the force kernel's code and the layout of the data it reads
+# (the list build writes the rows and masks): a DRAM-traffic figure measured on one
+# build of the force kernel stays valid while these are unchanged.
+FORCE_SOURCES = ("rbl_force_kernel.cuh", "rbl_force.cu", "rbl_internal.cuh", "rbl_erfc_fit.cuh", "rbl_build.cu")
+
+
+def _digest(files) -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in sorted(_deps()):
-        if f.endswith(("_build.py",)):
-            continue
+    for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def source_digest() -> str:
+    """sha256 of the library sources (identifies the kernels a profile was taken on)."""
+    return _digest([f for f in _deps() if not f.endswith("_build.py")])
+
+
+def force_digest() -> str:
+    """sha256 of the force kernel's sources and the list build's (see FORCE_SOURCES)."""
+    return _digest([os.path.join(CSRC, f) for f in FORCE_SOURCES])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -25,6 +25,10 @@ namespace {
 const double kPi = 3.14159265358979323846264338327950288;
 constexpr long long kMaxSlots = 1ll << 30;  // particle slots of a context (int indices, int32 rows)
 
+// Byte offset of the rbl_obs[R] area in the staging buffer: after the kinetic
+// partials (4 doubles per tile).
+size_t obs_staging_offset(int ntile) { return ((size_t)ntile * 32 + 255) & ~(size_t)255; }
+
 // Sizes and offsets of every array of a context's workspace.
 struct Plan {
     size_t off[40];
@@ -176,7 +180,8 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     const size_t Nq = p->potential == RBL_POT_LJ_EWALD ? Nz : 0; // charges only with the Ewald term
     size_t st = 48 * (size_t)n_real;                   // packed x and v (host copies)
     if (st < 4 * Nz * (size_t)(p->p + 1)) st = 4 * Nz * (size_t)(p->p + 1); // batch hook
-    if (st < (size_t)P.ntile * 32) st = (size_t)P.ntile * 32;               // kinetic partials
+    if (st < obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R)       // kinetic partials, then rbl_obs[R]
+        st = obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R;
     if (st < (1u << 20)) st = 1u << 20;
     P.staging_bytes = st;
     const size_t sizes[] = {
@@ -705,7 +710,8 @@ rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device)
     return RBL_OK;
 }
 
-rbl_status rbl_step(rbl_ctx *ctx, int n)
+// n steps; sync: wait for them and report the device flags.
+static rbl_status step_impl(rbl_ctx *ctx, int n, bool sync)
 {
     if (!ctx || n < 0) return RBL_EINVAL;
     if (n == 0) return RBL_OK;
@@ -752,43 +758,44 @@ rbl_status rbl_step(rbl_ctx *ctx, int n)
     ctx->step += n;
     ctx->force_valid = 1;
     ctx->energy_valid = 1;
-    return check_flags(ctx);
+    return sync ? check_flags(ctx) : RBL_OK;
 }
 
+rbl_status rbl_step(rbl_ctx *ctx, int n) { return step_impl(ctx, n, true); }
+
+rbl_status rbl_step_async(rbl_ctx *ctx, int n)
+{
+    if (ctx && ctx->phase_timing) return step_impl(ctx, n, true); // timed steps wait for their events
+    return step_impl(ctx, n, false);
+}
+
+
+// Enqueues the kinetic sums, the device-side assembly of rbl_obs[R] (after the
+// kinetic partials in the staging area) and its copy to out.
+rbl_status enqueue_observables(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
+{
+    rbl_status st = ensure_force(ctx, true);
+    if (st != RBL_OK) return st;
+    CK(launch_kinetic(ctx->view, ctx->stream));
+    rbl_obs *dev = (rbl_obs *)((char *)ctx->view.staging + obs_staging_offset(ctx->view.ntile));
+    CK(launch_obs(ctx->view, dev, ctx->prm.r_s, ctx->stream));
+    CK(cudaMemcpyAsync(out, dev, sizeof(rbl_obs) * (size_t)ctx->R,
+                       ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    return RBL_OK;
+}
 
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out)
 {
     if (!ctx || !out) return RBL_EINVAL;
-    rbl_status st = ensure_force(ctx, true);
+    rbl_status st = enqueue_observables(ctx, out, 0);
     if (st != RBL_OK) return st;
-    CK(launch_kinetic(ctx->view, ctx->stream));
-    st = check_flags(ctx, true);
-    if (st != RBL_OK) return st;
-    const double rs = ctx->prm.r_s, i3 = 1.0 / (rs * rs * rs), i9 = i3 * i3 * i3;
-    for (int r = 0; r < ctx->R; ++r) {
-        const RepScalars &s = ctx->h_rs[r];
-        const Box &b = ctx->h_box[r];
-        const double V = b.L[0] * b.L[1] * b.L[2];
-        const double rho = b.N / V;
-        rbl_obs &o = out[r];
-        std::memset(&o, 0, sizeof(o));
-        o.U_est = s.energy;
-        o.W_est = s.virial;
-        o.K = 0.5 * s.ksum;
-        o.T_kin = s.ksum / (3.0 * b.N);
-        o.P = rho * o.T_kin + s.virial / (3.0 * V);
-        o.U_tail = 8.0 / 3.0 * kPi * rho * (i9 / 3.0 - i3);
-        o.P_tail = 16.0 / 3.0 * kPi * rho * rho * (2.0 * i9 / 3.0 - i3);
-        for (int a = 0; a < 3; ++a) o.net_momentum[a] = s.psum[a];
-        o.step = (long long)ctx->h_sc->step;
-        o.n_rebuild = s.n_rebuild;
-        o.Ns_mean = (double)s.ns_sum / b.N;
-        o.Nc_mean = (double)s.nc_sum / b.N;
-        o.Mc_mean = (double)s.m_sum / b.N;
-        o.Ns_max = s.ns_max;
-        o.Nc_max = s.nc_max;
-    }
-    return RBL_OK;
+    return check_flags(ctx, true);
+}
+
+rbl_status rbl_observables_async(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
+{
+    if (!ctx || !out) return RBL_EINVAL;
+    return enqueue_observables(ctx, out, ptr_is_device);
 }
 
 rbl_status rbl_exact_energy(rbl_ctx *ctx, double *U, double *W)

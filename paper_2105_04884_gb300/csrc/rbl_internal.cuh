@@ -607,6 +607,7 @@ cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
 cudaError_t launch_kinetic(const View &v, cudaStream_t s);
+cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);

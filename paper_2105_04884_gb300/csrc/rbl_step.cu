@@ -333,6 +333,48 @@ cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t 
     return cudaGetLastError();
 }
 
+// rbl_obs of every replica from its scalars (kinetic sums, energy and virial of the
+// last force evaluation, list statistics): out[R], for rbl_observables and its
+// asynchronous form alike.  Explicitly rounded operations, no contraction.
+__global__ void k_obs(View v, rbl_obs *out, double rs)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= v.R) return;
+    const double pi = 3.14159265358979323846;
+    const RepScalars &s = v.rs[r];
+    const Box &b = v.box[r];
+    const double n = (double)b.N;
+    const double V = __dmul_rn(__dmul_rn(b.L[0], b.L[1]), b.L[2]);
+    const double rho = __ddiv_rn(n, V);
+    const double i3 = __ddiv_rn(1.0, __dmul_rn(__dmul_rn(rs, rs), rs));
+    const double i9 = __dmul_rn(__dmul_rn(i3, i3), i3);
+    rbl_obs o;
+    o.U_est = s.energy;
+    o.W_est = s.virial;
+    o.K = __dmul_rn(0.5, s.ksum);
+    o.T_kin = __ddiv_rn(s.ksum, __dmul_rn(3.0, n));
+    o.P = __dadd_rn(__dmul_rn(rho, o.T_kin), __ddiv_rn(s.virial, __dmul_rn(3.0, V)));
+    // per-particle energy and pressure tails of the truncated LJ fluid (Sec. 3)
+    o.U_tail = __dmul_rn(__dmul_rn(__dmul_rn(__ddiv_rn(8.0, 3.0), pi), rho), __dsub_rn(__ddiv_rn(i9, 3.0), i3));
+    o.P_tail = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__ddiv_rn(16.0, 3.0), pi), rho), rho),
+                         __dsub_rn(__ddiv_rn(__dmul_rn(2.0, i9), 3.0), i3));
+    for (int a = 0; a < 3; ++a) o.net_momentum[a] = s.psum[a];
+    o.step = (long long)v.sc->step;
+    o.n_rebuild = s.n_rebuild;
+    o.Ns_mean = __ddiv_rn((double)s.ns_sum, n);
+    o.Nc_mean = __ddiv_rn((double)s.nc_sum, n);
+    o.Mc_mean = __ddiv_rn((double)s.m_sum, n);
+    o.Ns_max = s.ns_max;
+    o.Nc_max = s.nc_max;
+    out[r] = o;
+}
+
+cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s)
+{
+    k_obs<<<ceil_div(v.R, 128), 128, 0, s>>>(v, out, rs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kinetic(const View &v, cudaStream_t s)
 {
     int g = ceil_div(v.N, kBlock);

@@ -60,11 +60,11 @@ class rbl_obs(ctypes.Structure):
 
 
 EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch", "rbl_create",
-           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_set_charges", "rbl_get_state", "rbl_build_lists",
-           "rbl_forces", "rbl_step", "rbl_observables", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows",
-           "rbl_get_batch", "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config",
-           "rbl_autotune", "rbl_set_phase_timing", "rbl_phase_times",
-           "rbl_forces_static", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
+           "rbl_create_batch", "rbl_replicas", "rbl_set_state", "rbl_set_charges", "rbl_get_state",
+           "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_step_async", "rbl_observables",
+           "rbl_observables_async", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows", "rbl_get_batch",
+           "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config", "rbl_autotune", "rbl_set_phase_timing",
+           "rbl_phase_times", "rbl_forces_static", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
 
 _lib = None
 
@@ -98,7 +98,9 @@ def load(build_if_missing: bool = False):
     L.rbl_build_lists.argtypes = [P]
     L.rbl_forces.argtypes = [P, P, I]
     L.rbl_step.argtypes = [P, I]
+    L.rbl_step_async.argtypes = [P, I]
     L.rbl_observables.argtypes = [P, ctypes.POINTER(rbl_obs)]
+    L.rbl_observables_async.argtypes = [P, P, I]
     L.rbl_exact_energy.argtypes = [P, P, P]
     L.rbl_get_lists.argtypes = [P, I, P, I, P]
     L.rbl_get_rows.argtypes = [P, I, P, I, P, I, P]
@@ -253,10 +255,34 @@ class _Context:
     def step(self, n=1):
         self._check(self.lib.rbl_step(self.h, int(n)))
 
+    def step_async(self, n=1):
+        """Enqueue n steps without waiting (errors surface at the next synchronising call)."""
+        self._check(self.lib.rbl_step_async(self.h, int(n)))
+
     def _observables(self):
         o = (rbl_obs * self.R)()
         self._check(self.lib.rbl_observables(self.h, o))
         return [o[r].as_dict() for r in range(self.R)]
+
+    def observables_async(self, out):
+        """Enqueue the observables into `out` (a page-locked uint8 tensor or array of
+        R * sizeof(rbl_obs) bytes, e.g. from obs_buffer()) without waiting; read it
+        with read_obs() after the stream has synchronised."""
+        dev = self._is_dev(out)
+        self._check(self.lib.rbl_observables_async(self.h, _ptr(out), int(dev)))
+
+    def obs_buffer(self, pinned=True):
+        """A host buffer for observables_async (page-locked by default)."""
+        return self._torch.empty(self.R * ctypes.sizeof(rbl_obs), dtype=self._torch.uint8, pin_memory=pinned)
+
+    def read_obs(self, buf):
+        """Dicts from a buffer filled by observables_async (call after synchronising)."""
+        raw = bytes(buf.numpy().tobytes()) if hasattr(buf, "numpy") else bytes(buf)
+        arr = (rbl_obs * self.R).from_buffer_copy(raw)
+        return [arr[r].as_dict() for r in range(self.R)]
+
+    def synchronize(self):
+        self.stream.synchronize()
 
     def _exact_energy(self):
         U = np.zeros(self.R)
