@@ -74,6 +74,38 @@ def dist_info():
     return rank, world, local
 
 
+# Multi-GPU: one independent replica per rank (weak scaling, no collective on the data
+# path); the only collectives are the barriers around the timed region and the max of
+# the ranks' times.
+def replica_seed(rank):
+    return 1 + rank
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(t, world, device):
+    """The slowest rank's time (every rank gets it)."""
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(n_per_rank, steps, world, ms):
+    """Particle-steps per second of the whole job: every rank's particles over the
+    slowest rank's time."""
+    return n_per_rank * steps * world / (ms * 1e-3)
+
+
 class Clocks:
     """nvidia-smi sampler during the timed region."""
 
@@ -256,7 +288,7 @@ def physics_compare(a, b, dr):
 ENSEMBLE = dict(R=256, rc=1.5, rs=3.5, skin=0.3, p=10, dt=0.005, gamma=1.0, K=2)
 
 
-def ensemble_bench(a, rank, timed):
+def ensemble_bench(a, rank, world, timed):
     """Batched ensemble: 256 replicas, N log-uniform in [500, 20000], rho* in
     [0.6, 0.9], T* in [1, 2], FP32, one launch per kernel for all replicas and one
     graph per step; beside it the same replicas as 256 separate contexts stepped
@@ -266,7 +298,7 @@ def ensemble_bench(a, rank, timed):
     from paper_2105_04884_gb300 import inputs, rbl
 
     e = ENSEMBLE
-    reps = inputs.ensemble(e["R"], seed=1 + rank)
+    reps = inputs.ensemble(e["R"], seed=replica_seed(rank))
     shared = dict(r_c=e["rc"], r_s=e["rs"], skin=e["skin"], p=e["p"], dt=e["dt"], gamma=e["gamma"],
                   cells_per_cutoff=e["K"], precision=rbl.RBL_FP32)
     ntot = sum(rp.N for rp in reps)
@@ -292,7 +324,7 @@ def ensemble_bench(a, rank, timed):
     del singles
     torch.cuda.empty_cache()
     return {"workload": "lj_ensemble_R256_N500-20000_rho0.6-0.9_T1-2_rc1.5_rs3.5_p10_nvt", "replicas": e["R"],
-            "particles": ntot, "steps": K, "value": ntot * K / (ms * 1e-3), "unit": "particle-steps/s",
+            "particles": ntot, "steps": K, "value": whole_job_rate(ntot, K, world, ms), "unit": "particle-steps/s",
             "ms_per_step": ms / K, "rebuilds_per_replica_mean": sum(o["n_rebuild"] for o in obs) / e["R"],
             "launch_config": ens_cfg,
             "separate_contexts": {"value": ntot * k / t_single, "steps": k,
@@ -303,7 +335,7 @@ SLAB = dict(N=4194304, rho_l=0.75, rho_v=0.01, frac=0.4, T=0.9, rc=1.5, rs=4.0, 
             gamma=1.0, K=2, steps=500, dz=0.5)
 
 
-def slab_bench(a, rank, timed):
+def slab_bench(a, rank, world, timed):
     """Liquid-vapour slab: N = 4,194,304 in Lx = Ly, Lz = 4 Lx, liquid rho* = 0.75
     over the central 40% of z, vapour 0.01 elsewhere, T* = 0.9, r_c = 1.5, r_s = 4.0,
     p = 20, FP32; 500 steps of RBL and of the full list from the same start, then
@@ -317,11 +349,11 @@ def slab_bench(a, rank, timed):
     c = SLAB
     V = c["N"] / (c["rho_l"] * c["frac"] + c["rho_v"] * (1.0 - c["frac"]))
     Lx = (V / 4.0) ** (1.0 / 3.0)
-    x, L = inputs.slab(c["N"], Lx, 4.0 * Lx, c["rho_l"], c["rho_v"], c["frac"], seed=1 + rank)
-    v = inputs.maxwell_boltzmann(len(x), c["T"], seed=1 + rank)
+    x, L = inputs.slab(c["N"], Lx, 4.0 * Lx, c["rho_l"], c["rho_v"], c["frac"], seed=replica_seed(rank))
+    v = inputs.maxwell_boltzmann(len(x), c["T"], seed=replica_seed(rank))
     nb = int(round(L[2] / c["dz"]))
     common = dict(r_c=c["rc"], r_s=c["rs"], skin=c["skin"], p=c["p"], dt=c["dt"], T=c["T"], gamma=c["gamma"],
-                  seed=1 + rank, cells_per_cutoff=c["K"], precision=rbl.RBL_FP32, rho_cap=c["rho_l"])
+                  seed=replica_seed(rank), cells_per_cutoff=c["K"], precision=rbl.RBL_FP32, rho_cap=c["rho_l"])
     out = {"workload": "lj_slab_N4194304_rhoL0.75_rhoV0.01_T0.9_rc1.5_rs4.0_p20_nvt", "N": len(x),
            "box": [float(L[0]), float(L[1]), float(L[2])], "steps": c["steps"]}
     prof = {}
@@ -335,7 +367,7 @@ def slab_bench(a, rank, timed):
             s.step(10)
             s.density_profile(2, nb, h)
         prof[name] = h / 5.0 / (L[0] * L[1] * c["dz"])
-        out[name] = {"value": len(x) * c["steps"] / (ms * 1e-3), "unit": "particle-steps/s",
+        out[name] = {"value": whole_job_rate(len(x), c["steps"], world, ms), "unit": "particle-steps/s",
                      "ms_per_step": ms / c["steps"], "T_kin": s.observables()["T_kin"]}
         del s
         torch.cuda.empty_cache()
@@ -555,7 +587,7 @@ def ewald_bench(a, world, x, v, L, common, timed):
         s.autotune(trials=3)
         _, (pm, n) = timed(s, a.steps, phases=True)
         ms, _ = timed(s, a.steps, phases=False)
-        out[name] = {"value": N * a.steps * world / (ms * 1e-3), "ms_per_step": ms / a.steps,
+        out[name] = {"value": whole_job_rate(N, a.steps, world, ms), "ms_per_step": ms / a.steps,
                      "force_kernel_ms": pm[2] / n, "rebuild_chain_ms": pm[1] / n}
         del s
         torch.cuda.empty_cache()
@@ -586,28 +618,15 @@ def run_ours(a, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     w = WORKLOAD
     N = a.N
-    x, v, L = make_workload(N, 1 + rank)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-
-    def max_over_ranks(t):
-        if world == 1:
-            return t
-        import torch.distributed as dist
-
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+    x, v, L = make_workload(N, replica_seed(rank))
+    sync_all = lambda: barrier(world)  # noqa: E731
+    slowest = lambda t: max_over_ranks(t, world, dev)  # noqa: E731
 
     def timed(system, K, phases=True):
         system.set_phase_timing(phases)
         system.phase_times(reset=True)
         stream = system.stream
-        barrier()
+        sync_all()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -617,19 +636,19 @@ def run_ours(a, rank, world, local):
         torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
-        barrier()
+        sync_all()
         ms = e0.elapsed_time(e1)
-        return max_over_ranks(ms), system.phase_times()
+        return slowest(ms), system.phase_times()
 
     common = dict(r_c=w["rc"], r_s=w["rs"], skin=w["skin"], p=w["p"], dt=w["dt"], T=w["T"], gamma=w["gamma"],
-                  seed=1 + rank, cells_per_cutoff=w["K"], precision=rbl.RBL_FP32)
+                  seed=replica_seed(rank), cells_per_cutoff=w["K"], precision=rbl.RBL_FP32)
     ewald = a.potential == "ewald"
     wname, kname, qself = w["name"], FORCE_KERNEL, 0
     if ewald:  # the charged fluid is the timed workload (every block below runs it)
         from paper_2105_04884_gb300 import inputs
 
         common.update(potential=rbl.RBL_POT_LJ_EWALD, alpha=EWALD_ALPHA,
-                      charges=inputs.charges(N, 1.0, seed=1 + rank))
+                      charges=inputs.charges(N, 1.0, seed=replica_seed(rank)))
         wname = "charged_" + w["name"] + "_ewald_alpha%g" % EWALD_ALPHA
         kname, qself = FORCE_KERNEL_EWALD, 4
     s = rbl.System(x, v, L, **common)
@@ -644,7 +663,7 @@ def run_ours(a, rank, world, local):
     ms, _ = timed(s, a.steps, phases=False)
     clk = clocks.stop()
     obs = s.observables()
-    value = N * a.steps * world / (ms * 1e-3)
+    value = whole_job_rate(N, a.steps, world, ms)
     rebuilds = obs["n_rebuild"] - obs1["n_rebuild"]
 
     # roofline of the force kernel: algorithmic bytes per particle of the data it must
@@ -695,7 +714,7 @@ def run_ours(a, rank, world, local):
         sf.autotune(trials=3)
         _, (pmf, nf) = timed(sf, a.steps, phases=True)
         msf, _ = timed(sf, a.steps, phases=False)
-        vf = N * a.steps * world / (msf * 1e-3)
+        vf = whole_job_rate(N, a.steps, world, msf)
         of = sf.observables()
         result["full_list"] = {"value": vf, "ms_per_step": msf / a.steps,
                                "force_kernel_ms": pmf[2] / nf, "full_mean": of["Ns_mean"]}
@@ -709,7 +728,7 @@ def run_ours(a, rank, world, local):
         s2.autotune(trials=3)
         _, (pm2, n2) = timed(s2, a.steps, phases=True)
         ms2, _ = timed(s2, a.steps, phases=False)
-        v2 = N * a.steps * world / (ms2 * 1e-3)
+        v2 = whole_job_rate(N, a.steps, world, ms2)
         result["rbl_rc2.0"] = {"value": v2, "ms_per_step": ms2 / a.steps, "force_kernel_ms": pm2[2] / n2,
                                "speedup_vs_full_list": v2 / vf}
         del s2
@@ -722,7 +741,7 @@ def run_ours(a, rank, world, local):
         _, (pm3, n3) = timed(s3, a.steps, phases=True)
         ms3, _ = timed(s3, a.steps, phases=False)
         o3 = s3.observables()
-        v3 = N * a.steps * world / (ms3 * 1e-3)
+        v3 = whole_job_rate(N, a.steps, world, ms3)
         result["rbl_stencil_pool"] = {"value": v3, "ms_per_step": ms3 / a.steps,
                                       "phases_ms_per_step": {"integrate": pm3[0] / n3, "rebuild_chain": pm3[1] / n3,
                                                              "force_kernel": pm3[2] / n3, "force_reduce": pm3[3] / n3},
@@ -750,7 +769,7 @@ def run_ours(a, rank, world, local):
         obs_c = rbl.rbl_obs()
         e2e = {}
         for mode in ("async", "sync"):
-            barrier()
+            sync_all()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()), 0,
@@ -769,25 +788,26 @@ def run_ours(a, rank, world, local):
                 obs_all = (rbl.rbl_obs * a.steps).from_buffer_copy(ring.numpy().tobytes())
                 t_mean = sum(o.T_kin for o in obs_all) / a.steps
             torch.cuda.synchronize()
-            e2e[mode] = max_over_ranks(time.perf_counter() - t0)
-            barrier()
+            e2e[mode] = slowest(time.perf_counter() - t0)
+            sync_all()
         te = e2e["async"]
-        result["e2e"] = {"value": N * a.steps * world / te, "unit": "particle-steps/s",
+        result["e2e"] = {"value": whole_job_rate(N, a.steps, world, te * 1e3), "unit": "particle-steps/s",
                          "h2d_bytes_per_step": 48 * N / a.steps,
                          "d2h_bytes_per_step": 48 * N / a.steps + osz,
                          "path": "rbl_set_state(host) + steps x (rbl_step_async(1) + rbl_observables_async into "
                                  "a page-locked ring) + rbl_get_state(host, waits and reports device flags) + host "
                                  "read of every step's rbl_obs",
                          "T_kin_mean": t_mean}
-        result["e2e_sync"] = {"value": N * a.steps * world / e2e["sync"], "unit": "particle-steps/s",
+        result["e2e_sync"] = {"value": whole_job_rate(N, a.steps, world, e2e["sync"] * 1e3),
+                              "unit": "particle-steps/s",
                               "path": "as e2e with rbl_step(1) and rbl_observables, each of which waits"}
         del se
     if not a.no_ewald and not ewald:
         result["ewald"] = ewald_bench(a, world, x, v, L, common, timed)
     if not a.no_ensemble:
-        result["ensemble"] = ensemble_bench(a, rank, timed)
+        result["ensemble"] = ensemble_bench(a, rank, world, timed)
     if not a.no_slab:
-        result["slab"] = slab_bench(a, rank, timed)
+        result["slab"] = slab_bench(a, rank, world, timed)
     if rank == 0 and not a.no_physics:
         # the bench workload's (r_c, p) and r_c = 2.0 (the matched setting), each
         # against one full-list trajectory
