@@ -282,6 +282,12 @@ __global__ void k_copy_back(View v, int conditional)
 // itself; the segment table still spans the whole stencil, for the batch.
 constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
+// LIST: kListShell (core row + shell mask), kListFull (full-list mask), kListPool
+// (core row only; stencil-pool sampling), fixed at compile time so that the pair-test
+// loop carries no mode branches.
+enum { kListShell = 0, kListFull = 1, kListPool = 2 };
+
+template <int LIST>
 __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int conditional)
 {
     if (skip(v, conditional)) return;
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     // next build, however far the particle drifts meanwhile
     for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
     RepScalars &rsc = v.rs[r];
-    const bool pool = v.sampling != 0; // no masks: the stencil population is not bounded by them
+    constexpr bool pool = LIST == kListPool; // no masks: the stencil population is not bounded by them
     if (!pool && M > v.Mcap) {
         // too many candidates for the masks: flag it and leave these particles with
         // empty rows so that no kernel decodes a mask that was not written
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
         Mloop = pre[nseg];
     }
     const int nchunk = (Mloop + 31) >> 5;
-    const bool full = v.full_list != 0;
+    constexpr bool full = LIST == kListFull;
     const size_t N = (size_t)v.N;
     int wmc = 0, wms = 0;
     unsigned long long wsc = 0ull, wss = 0ull;
@@ -422,21 +428,17 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             for (int q = 0; q < mm; ++q) {
                 PairGeom g = pair_geom(s_pos[warp][q], pj, h);
                 const bool other = valid && j != base + q;
-                bool in_core, in_shell;
-                if (full) {
-                    in_core = false;
-                    in_shell = other && g.r2 < v.t_cut_list;
-                } else if (pool) {
-                    in_core = other && g.r2 < v.t_core_list;
-                    in_shell = false;
-                } else {
-                    in_core = other && g.r2 < v.t_core_list;
-                    in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
+                if constexpr (!pool) {
+                    const bool in_shell = full ? other && g.r2 < v.t_cut_list
+                                               : other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
+                    const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
+                    my_shell = lane == q ? bs : my_shell;
                 }
-                const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
-                const unsigned bc = __ballot_sync(0xffffffffu, in_core);
-                my_shell = lane == q ? bs : my_shell;
-                my_core = lane == q ? bc : my_core;
+                if constexpr (!full) {
+                    const bool in_core = other && g.r2 < v.t_core_list;
+                    const unsigned bc = __ballot_sync(0xffffffffu, in_core);
+                    my_core = lane == q ? bc : my_core;
+                }
             }
             __syncwarp();
             if (lane < mm) {
@@ -518,7 +520,10 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_sort_cells<<<gC, kBlock, 0, s>>>(v, cond);
     k_permute<<<gN, kBlock, 0, s>>>(v, cond);
     k_copy_back<<<gN, kBlock, 0, s>>>(v, cond);
-    k_build_lists<<<ceil_div(v.ncell, v.build_warps), v.build_warps * 32, 0, s>>>(v, cond);
+    const dim3 gB(ceil_div(v.ncell, v.build_warps)), bB(v.build_warps * 32);
+    if (v.sampling) k_build_lists<kListPool><<<gB, bB, 0, s>>>(v, cond);
+    else if (v.full_list) k_build_lists<kListFull><<<gB, bB, 0, s>>>(v, cond);
+    else k_build_lists<kListShell><<<gB, bB, 0, s>>>(v, cond);
     k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
     k_finish_all<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();
