@@ -333,7 +333,8 @@ __global__ void __maxnreg__(FP32 ? (EWALD ? kForceRegsEwald : kForceRegs) : 128)
                     if (q0 < nb) {
                         int jj[kGather];
 #pragma unroll
-                        for (int u = 0; u < kGather; ++u) jj[u] = J[q0 + u];
+                        for (int u = 0; u < kGather; ++u) // slots past the batch: unused
+                            jj[u] = q0 + u < PMAX ? J[q0 + u] : i;
                         acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
                     }
                 }
@@ -401,7 +402,8 @@ __global__ void __maxnreg__(FP32 ? (EWALD ? kForceRegsEwald : kForceRegs) : 128)
                     if (q0 < nb) {
                         int jj[kGather];
 #pragma unroll
-                        for (int u = 0; u < kGather; ++u) jj[u] = J[q0 + u];
+                        for (int u = 0; u < kGather; ++u) // slots past the batch: unused
+                            jj[u] = q0 + u < PMAX ? J[q0 + u] : i;
                         acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
                     }
                 }
