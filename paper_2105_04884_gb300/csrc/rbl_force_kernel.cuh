@@ -202,24 +202,28 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 // Memory-level parallelism: the mask words of a thread are staged in shared memory
 // with bursts of independent loads (column-major storage makes every burst coalesced
 // across the warp), the batch is drawn while those loads are in flight, and
-// neighbour indices and positions are gathered kGather at a time before their pair
+// neighbour indices and positions are gathered `gather` at a time before their pair
 // terms are computed.
 // Threads per block: a launch parameter of the context (64, 128 or 256; chosen by
 // rbl_autotune); the staging arrays are dynamic shared memory sized for the block.
-// FP32 registers are capped so that 7 blocks of 128 threads fit an SM (5 with the
-// Ewald term; the FP64 path needs more and runs at the FP64 rate anyway).
-#ifndef RBL_FORCE_REGS
-#define RBL_FORCE_REGS 72
-#endif
-constexpr int kForceRegs = RBL_FORCE_REGS;
-constexpr int kForceRegsEwald = 80; // the Ewald term needs more: 6 blocks of 128 threads per SM
 static_assert(kMinBlock == 64 && kMaxForceThreads % 64 == 0, "per-block partials are sized for kMinBlock");
 constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
-constexpr int kGather = 8;
+
+// Gather width and FP32 register cap per mode, measured on GB300 (RBL step on the
+// LJ fluid at N = 2^20, best block shape of each): shell sampling and the full list
+// run fastest with 4 gathers in flight and 64 registers (4 blocks of 256 threads per
+// SM), the stencil pool with 12 and 80; the Ewald term needs 80 registers and keeps
+// 8.  The FP64 path needs 128 registers and runs at the FP64 rate anyway.
+template <int MODE, bool EWALD>
+struct ForceTuning {
+    static constexpr int gather = EWALD ? 8 : (MODE == 3 ? 12 : 4);
+    static constexpr int regs = EWALD ? 80 : (MODE == 3 ? 80 : 64);
+};
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>
-__global__ void __maxnreg__(FP32 ? (EWALD ? kForceRegsEwald : kForceRegs) : 128) k_force(View v, int step_offset)
+__global__ void __maxnreg__((FP32 ? ForceTuning<MODE, EWALD>::regs : 128)) k_force(View v, int step_offset)
 {
+    constexpr int kGather = ForceTuning<MODE, EWALD>::gather;
     // staged mask words [kMaskStage][blockDim] and the set bits before each of them
     extern __shared__ unsigned s_dyn[];
     const int bd = blockDim.x;
