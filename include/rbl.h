@@ -265,7 +265,7 @@ rbl_status rbl_rdf(rbl_ctx *ctx, float dr, int nbins, long long *hist);
 rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *hist);
 
 /* Launch shapes, which no result depends on (the tests check this bit for bit):
- * threads per block of the force kernel (64, 128 or 256; default 256 for FP32 LJ with
+ * threads per block of the force kernel (64, 128 or 256; default 256 for FP32 with
  * shell sampling or the full list, 128 otherwise) and home
  * cells (warps) per block of the list build (2, 4 or 8; default 4).
  * rbl_autotune times every candidate of each on the current state (`trials`

@@ -267,7 +267,7 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.ka32 = (float)v.ka;
     // the force kernel's fastest block before any autotuning: 256 threads for FP32
     // shell sampling and the full list, 128 otherwise (measured at N = 2^20)
-    v.force_threads = (prm->precision == RBL_FP32 && !prm->sampling && prm->potential == RBL_POT_LJ) ? 256 : 128;
+    v.force_threads = (prm->precision == RBL_FP32 && !prm->sampling) ? 256 : 128;
     v.build_warps = 4;
     v.ncell = P.ncell;
     const double rc = prm->r_c, rs = prm->r_s, sk = prm->skin;

@@ -209,15 +209,16 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 static_assert(kMinBlock == 64 && kMaxForceThreads % 64 == 0, "per-block partials are sized for kMinBlock");
 constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
 
-// Gather width and FP32 register cap per mode, measured on GB300 (RBL step on the
-// LJ fluid at N = 2^20, best block shape of each): shell sampling and the full list
-// run fastest with 4 gathers in flight and 64 registers (4 blocks of 256 threads per
-// SM), the stencil pool with 12 and 80; the Ewald term needs 80 registers and keeps
-// 8.  The FP64 path needs 128 registers and runs at the FP64 rate anyway.
+// Gather width and FP32 register cap per mode, measured on GB300 (the LJ fluid and
+// the charged fluid at N = 2^20, best block shape of each): shell sampling and the
+// full list, with or without the Ewald term, run fastest with 4 gathers in flight and
+// 64 registers (4 blocks of 256 threads per SM), the stencil pool with 12 and 80 (8
+// and 80 with the Ewald term).  The FP64 path needs up to 128 registers and runs at
+// the FP64 rate anyway.
 template <int MODE, bool EWALD>
 struct ForceTuning {
-    static constexpr int gather = EWALD ? 8 : (MODE == 3 ? 12 : 4);
-    static constexpr int regs = EWALD ? 80 : (MODE == 3 ? 80 : 64);
+    static constexpr int gather = MODE == 3 ? (EWALD ? 8 : 12) : 4;
+    static constexpr int regs = MODE == 3 ? 80 : 64;
 };
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>
