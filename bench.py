@@ -35,6 +35,7 @@ WORKLOAD = dict(name="lj_fluid_N1048576_rho0.8_T1.5_rc1.5_rs3.5_skin0.3_p10_nvt"
                 rc=1.5, rs=3.5, skin=0.3, p=10, dt=0.005, gamma=1.0, K=2)
 FORCE_KERNEL = "k_force<0, true, false, 10, false>"  # RBL, FP32, no energy, p = 10, LJ
 FORCE_KERNEL_EWALD = "k_force<0, true, false, 10, true>"  # the same with the Ewald real-space term
+EWALD_ALPHA = 1.0  # the charged fluid's splitting parameter: erfc(alpha r_s) = 7e-7 at r_s = 3.5
 
 
 def parse():
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--table1", action="store_true",
                     help="run the paper's Table 1 study (g(r) first peak and MSD slope, classical cutoffs vs RBL)")
     ap.add_argument("--table1-scale", type=float, default=1.0, help="fraction of the paper's step counts")
+    ap.add_argument("--ewald-physics", action="store_true",
+                    help="run the matched-physics comparison for the charged fluid (Ewald real-space term)")
     ap.add_argument("--physics", action="store_true",
                     help="run the full matched-physics sweep (r_c x p x precision vs the full list) instead")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="override particle count (debug only)")
@@ -193,11 +196,12 @@ PHYS = dict(N=32000, rho=0.8442, T=1.2, rs=3.5, skin=0.3, dt=0.005, gamma=1.0, K
             block=500, stride=10, rdf_every=5, dr=0.02)
 
 
-def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS, sampling=0):
+def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS, sampling=0, charges=None, alpha=0.0):
     """Block-averaged observables of one NVT trajectory.  Pressure and energy are the
     exact (unsampled) ones of the configurations the dynamics visits: P = rho T_kin +
     W / (3V) and U / N with W, U over every pair with r < r_s; the RBL estimates of the
-    same quantities are reported beside them.  g(r) from ordered-pair counts."""
+    same quantities are reported beside them.  g(r) from ordered-pair counts.
+    charges: the charged fluid (pair LJ + q_i q_j erfc(alpha r) / r)."""
     import numpy as np
 
     from paper_2105_04884_gb300 import rbl
@@ -205,9 +209,10 @@ def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS, sampling=0):
     N = len(x)
     V = float(np.prod(L))
     rho = N / V
+    pot = {} if charges is None else dict(potential=rbl.RBL_POT_LJ_EWALD, alpha=alpha, charges=charges)
     s = rbl.System(x, v, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
                    gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision, full_list=full,
-                   sampling=0 if full else sampling)
+                   sampling=0 if full else sampling, **pot)
     nbins = int(round(cfg["rs"] / cfg["dr"]))
     s.step(cfg["discard"])
     nblk = (cfg["steps"] - cfg["discard"]) // cfg["block"]
@@ -246,7 +251,7 @@ def physics_run(x, v, L, rc, p, precision, full, seed, cfg=PHYS, sampling=0):
         F_rbl = s.forces()
         ref = rbl.System(xs, vs, L, r_c=rc, r_s=cfg["rs"], skin=cfg["skin"], p=p, dt=cfg["dt"], T=cfg["T"],
                          gamma=cfg["gamma"], seed=seed, cells_per_cutoff=cfg["K"], precision=precision,
-                         full_list=True)
+                         full_list=True, **pot)
         F_ex = ref.forces()
         var = float(np.mean(np.sum((F_rbl - F_ex) ** 2, axis=1)))
         heating = {"force_err_var": var, "dT_predicted": cfg["dt"] * var / (6.0 * cfg["gamma"])}
@@ -415,6 +420,29 @@ def matched_physics_pair(rc=1.5, p=10, cfg=PHYS, full=None, sampling=0):
     return res, b
 
 
+def ewald_physics_sweep(alpha=EWALD_ALPHA):
+    """The matched-physics comparison for the charged fluid (the matched-physics system
+    with neutral random +-1 charges, pair LJ + q_i q_j erfc(alpha r) / r): RBL at
+    r_c in {1.5, 2.0, 2.5} x p in {10, 20} against the full list, FP32.  One JSON line
+    per run."""
+    from paper_2105_04884_gb300 import inputs, rbl
+
+    x, v, L = physics_inputs()
+    q = inputs.charges(len(x), 1.0, seed=1)
+    ch = dict(charges=q, alpha=alpha)
+    ref = physics_run(x, v, L, 1.5, 10, rbl.RBL_FP32, True, 1, **ch)
+    print(json.dumps({"potential": "lj+ewald", "alpha": alpha, "method": "full", "P": ref["P"], "U": ref["U"],
+                      "T": ref["T"], "wall_s": ref["wall_s"]}), flush=True)
+    for rc in (1.5, 2.0, 2.5):
+        for p in (10, 20):
+            r = physics_run(x, v, L, rc, p, rbl.RBL_FP32, False, 1, **ch)
+            c = physics_compare(r, ref, PHYS["dr"])
+            c.update({"potential": "lj+ewald", "alpha": alpha, "method": "rbl", "r_c": rc, "p": p,
+                      "wall_s": r["wall_s"], "n_rebuild": r["n_rebuild"],
+                      "heating": dict(r["heating"], dT_measured=r["T"][0] - ref["T"][0])})
+            print(json.dumps(c), flush=True)
+
+
 def physics_sweep():
     """The full study: r_c in {1.2, 1.5, 2.0} x p in {1, 2, 5, 10, 20}, FP32 and FP64,
     each against the full list of the same precision.  One JSON line per run."""
@@ -564,9 +592,6 @@ def variance_study(draws=8):
                                   "appendix_g1": fac * integ, "appendix_with_g": fac * integ_g,
                                   "ratio_meas_over_g": meas / (fac * integ_g)}), flush=True)
                 del s
-
-
-EWALD_ALPHA = 1.0  # erfc(alpha r_s) = 7e-7 at r_s = 3.5
 
 
 def ewald_bench(a, world, x, v, L, common, timed):
@@ -894,6 +919,10 @@ def main():
     if a.physics:
         if rank == 0:
             physics_sweep()
+        return
+    if a.ewald_physics:
+        if rank == 0:
+            ewald_physics_sweep()
         return
     if a.table1:
         if rank == 0:
