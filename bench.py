@@ -716,8 +716,9 @@ def run_ours(a, rank, world, local):
                    "timed_path": "rbl_step(K): CUDA graph replays, one per step (the rebuild chain behind a "
                                  "device-side IF node)"},
         # per step: integrate, the rebuild condition, force kernel and its reduction;
-        # the 12 rebuild-chain kernels on the steps that rebuild; the closing half-kick
-        "gpu_launches": 4 * a.steps + 12 * rebuilds + 1,
+        # the 12 rebuild-chain kernels on the steps that rebuild; on the last step the
+        # energy sums' chunk reduction and the closing half-kick
+        "gpu_launches": 4 * a.steps + 12 * rebuilds + 2,
         "phases_ms_per_step": {"integrate": phase_ms[0] / nsteps, "rebuild_chain": phase_ms[1] / nsteps,
                                "force_kernel": phase_ms[2] / nsteps, "force_reduce": phase_ms[3] / nsteps},
         "phase_timed_ms_per_step": ms_phase / a.steps,

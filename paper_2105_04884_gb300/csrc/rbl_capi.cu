@@ -34,7 +34,7 @@ struct Plan {
     size_t off[40];
     int n;
     size_t total;
-    int R, N, ntile, ncell, cap_c, W, S, Mcap, n_scan_blocks;
+    int R, N, ntile, ncell, cap_c, W, S, Mcap, n_scan_blocks, pchunks;
     long long n_real;
     size_t staging_bytes;
 };
@@ -154,12 +154,13 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
 {
     Plan P{};
     P.R = R;
-    long long slots = 0, cells = 0, n_real = 0;
+    long long slots = 0, cells = 0, n_real = 0, max_slots = 0;
     int S = 1, mcap = 32;
     double core_mean = 0.0;
     for (int r = 0; r < R; ++r) {
         Geo g = replica_geo(&prm[r], Ns[r]);
         slots += round_up_ll(Ns[r], kTile);
+        if (round_up_ll(Ns[r], kTile) > max_slots) max_slots = round_up_ll(Ns[r], kTile);
         cells += g.ncell + 1;
         n_real += Ns[r];
         S = g.S > S ? g.S : S;
@@ -176,6 +177,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.W = prm[0].sampling == RBL_SAMPLE_STENCIL ? 0 : P.Mcap / 32; // the stencil pool needs no masks
     P.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
     P.n_scan_blocks = (P.ncell + 2047) / 2048;
+    P.pchunks = (int)((max_slots / kMinBlock + kChunkGroups - 1) / kChunkGroups);
     const size_t Nz = (size_t)P.N;
     const size_t Nq = p->potential == RBL_POT_LJ_EWALD ? Nz : 0; // charges only with the Ewald term
     size_t st = 48 * (size_t)n_real;                   // packed x and v (host copies)
@@ -197,6 +199,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
         4 * Nz * (size_t)P.W, 4 * Nz,               // mask, n_shell
         4 * Nz,                                     // hcell
         64 * (Nz / kMinBlock),                      // partials [blocks][8] doubles, any block size >= kMinBlock
+        64 * (size_t)R * (size_t)P.pchunks,         // partials2 [R][pchunks][8] doubles
         sizeof(Box) * (size_t)R,                    // box
         8 * (size_t)P.ntile,                        // tile
         4 * (size_t)P.ncell,                        // cell_rep
@@ -305,6 +308,8 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.n_shell = (int *)(base + P.off[k++]);
     v.hcell = (int *)(base + P.off[k++]);
     v.partials = (double *)(base + P.off[k++]);
+    v.partials2 = (double *)(base + P.off[k++]);
+    v.pchunks = P.pchunks;
     v.box = (const Box *)(base + P.off[k++]);
     v.tile = (const int2 *)(base + P.off[k++]);
     v.cell_rep = (const int *)(base + P.off[k++]);

@@ -8,21 +8,53 @@ namespace rbl {
 
 namespace {
 
-// One block per replica: reduce its 64-thread groups' partials in a fixed order,
+// Second stage of the per-replica sums (FP64 forces, energies): block (c, r) adds
+// the partials of chunk c of replica r -- its 64-thread groups c*256 .. c*256+255 --
+// in a fixed tree, one group per thread, so the per-replica reduction reads one
+// entry per chunk instead of one per group and the work is spread over the GPU.
+// The tree depends on neither the force kernel's block size nor the ensemble.
+__global__ void __launch_bounds__(kChunkGroups) k_force_chunks(View v)
+{
+    const int c = blockIdx.x, r = blockIdx.y;
+    const Box &b = v.box[r];
+    const int g0 = b.first / kMinBlock, ng = b.slots / kMinBlock;
+    if (c * kChunkGroups >= ng) return; // block-uniform: past this replica's groups
+    const int g = c * kChunkGroups + (int)threadIdx.x;
+    double x[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) x[q] = g < ng ? v.partials[(size_t)(g0 + g) * 8 + q] : 0.0;
+    __shared__ double sh[5][kChunkGroups / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double s = warp_sum(x[q]);
+        if (lane == 0) sh[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+        for (int w = 0; w < kChunkGroups / 32; ++w) t += sh[threadIdx.x][w];
+        v.partials2[((size_t)r * v.pchunks + c) * 8 + threadIdx.x] = t;
+    }
+}
+
+// One block per replica: reduce its chunks' sums (k_force_chunks) in a fixed order,
 // form its mean force F_cor (Appendix A) and reset its integer accumulator for the
-// next evaluation.  bthreads: threads per partial (64).
-// exact = 1: store the unsampled energy and virial only (MODE 2 partials).
-__global__ void __launch_bounds__(kBlock) k_force_finish(View v, int bthreads, int fp32, int energy, int subtract,
-                                                         int advance, int exact)
+// next evaluation.  The FP32 path without energies reads no partials (its net force
+// is the exact integer sum).  exact = 1: store the unsampled energy and virial only
+// (MODE 2 partials).
+__global__ void __launch_bounds__(kBlock) k_force_finish(View v, int fp32, int energy, int subtract, int advance,
+                                                         int exact)
 {
     __shared__ double sh[5][kBlock / 32];
     const int r = blockIdx.x;
     const Box &b = v.box[r];
-    const int b0 = b.first / bthreads, nb = (fp32 && !energy) ? 0 : b.slots / bthreads;
+    const int ng = b.slots / kMinBlock;
+    const int nb = (fp32 && !energy) ? 0 : (ng + kChunkGroups - 1) / kChunkGroups;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] += v.partials[(size_t)(b0 + k) * 8 + q];
+        for (int q = 0; q < 5; ++q) acc[q] += v.partials2[((size_t)r * v.pchunks + k) * 8 + q];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -193,9 +225,9 @@ cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cud
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s)
 {
     bool fp32 = v.precision == RBL_FP32;
-    int threads = (fp32 && !energy) ? 32 : kBlock;
-    k_force_finish<<<v.R, threads, 0, s>>>(v, kMinBlock, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract,
-                                           advance, 0);
+    const bool sums = energy || !fp32; // FP64 force sums or energies to reduce
+    if (sums) k_force_chunks<<<dim3(v.pchunks, v.R), kChunkGroups, 0, s>>>(v);
+    k_force_finish<<<v.R, sums ? kBlock : 32, 0, s>>>(v, fp32 ? 1 : 0, sums ? 1 : 0, v.subtract, advance, 0);
     return cudaGetLastError();
 }
 
@@ -204,7 +236,8 @@ cudaError_t launch_exact_energy(const View &v, cudaStream_t s)
     cudaError_t e = v.potential == RBL_POT_LJ_EWALD ? launch_exact_energy_kernel_ewald(v, s)
                                                     : launch_exact_dispatch<false>(v, s);
     if (e != cudaSuccess) return e;
-    k_force_finish<<<v.R, kBlock, 0, s>>>(v, kMinBlock, 0, 1, 0, 0, 1);
+    k_force_chunks<<<dim3(v.pchunks, v.R), kChunkGroups, 0, s>>>(v);
+    k_force_finish<<<v.R, kBlock, 0, s>>>(v, 0, 1, 0, 0, 1);
     return cudaGetLastError();
 }
 

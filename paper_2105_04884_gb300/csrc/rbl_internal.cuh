@@ -19,6 +19,7 @@ constexpr int kMaxP = 128;         // largest batch size
 constexpr int kCellCap = 64;       // cells up to this size are sorted in local memory
 constexpr int kBlock = 256;        // threads per block of the per-particle kernels
 constexpr int kMinBlock = 64;      // smallest per-particle block: sizes the per-block partials
+constexpr int kChunkGroups = 256;  // 64-thread groups per second-stage chunk of the per-replica sums
 constexpr int kMaxStencil = 7;     // offsets per axis for K <= 3
 
 constexpr int kTile = 256;         // particle slots per tile; every replica starts on a tile
@@ -126,7 +127,9 @@ struct View {
     unsigned *mask;                 // mask[w * N + i], w < W
     int *n_shell;                   // set bits in the mask (N_s, or full-list length)
     int *hcell;                     // home cell (global index) of each particle at the last build
-    double *partials;               // [blocks][8]
+    double *partials;               // [64-thread groups][8]
+    double *partials2;              // [R][pchunks][8]: the groups' partials summed per chunk of 256
+    int pchunks;                    // chunks of the largest replica
     RepScalars *rs;                 // [R]
     DevScalars *sc;
     double *staging;                // host/device I/O scratch

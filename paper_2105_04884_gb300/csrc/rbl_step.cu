@@ -191,33 +191,30 @@ __device__ __forceinline__ T wsum(T x)
     return x;
 }
 
-// sum v^2 and sum v: per-block (= per-tile) partials in a fixed order, then one
-// block per replica.  Padding slots hold v = 0.
-__global__ void __launch_bounds__(kBlock) k_kinetic(View v)
+// sum v^2 and sum v per tile (256 slots): one warp per tile, each lane summing its
+// 8 slots in order before one fixed shuffle tree, so the FP64 tree is paid once
+// per 256 particles; per-tile partials in staging, reduced per replica in a fixed
+// order by k_kinetic_finish.  Padding slots hold v = 0.
+__global__ void __launch_bounds__(32) k_kinetic(View v)
 {
-    int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t N = (size_t)v.N;
+    const size_t base = (size_t)blockIdx.x * kTile + threadIdx.x;
     double x[4] = {0, 0, 0, 0};
-    if (i < v.N) {
-        size_t N = (size_t)v.N;
+#pragma unroll
+    for (int k = 0; k < kTile / 32; ++k) {
+        const size_t i = base + (size_t)k * 32;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double va = v.v[a * N + i];
-            x[0] += va * va;
-            x[1 + a] = va;
+            const double va = v.v[a * N + i];
+            x[0] = fma(va, va, x[0]);
+            x[1 + a] += va;
         }
     }
-    __shared__ double sh[4][kBlock / 32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        double s = wsum(x[k]);
-        if (lane == 0) sh[k][wid] = s;
-    }
-    __syncthreads();
+    for (int k = 0; k < 4; ++k) x[k] = wsum(x[k]);
     if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
-        v.staging[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+        const double out = threadIdx.x == 0 ? x[0] : threadIdx.x == 1 ? x[1] : threadIdx.x == 2 ? x[2] : x[3];
+        v.staging[(size_t)blockIdx.x * 4 + threadIdx.x] = out;
     }
 }
 
@@ -377,8 +374,7 @@ cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s)
 
 cudaError_t launch_kinetic(const View &v, cudaStream_t s)
 {
-    int g = ceil_div(v.N, kBlock);
-    k_kinetic<<<g, kBlock, 0, s>>>(v);
+    k_kinetic<<<v.ntile, 32, 0, s>>>(v);
     k_kinetic_finish<<<v.R, kBlock, 0, s>>>(v);
     return cudaGetLastError();
 }

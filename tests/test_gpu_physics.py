@@ -46,3 +46,33 @@ def test_heating_follows_estimator_variance(runs):
     pred = rc15["heating"]["dT_predicted"]
     assert dT > 10 * (rc15["T"][1] + full["T"][1])
     assert abs(dT - pred) < 0.3 * pred, (dT, pred)
+
+
+@pytest.fixture(scope="module")
+def charged_runs():
+    """The same system with neutral random +-1 charges and the Ewald real-space term
+    (alpha = 1): full list, RBL at r_c = 2.5 and at r_c = 1.5 (p = 10)."""
+    from paper_2105_04884_gb300 import inputs
+
+    x, v, L = bench.physics_inputs(cfg=CFG)
+    ch = dict(charges=inputs.charges(len(x), 1.0, seed=1), alpha=1.0)
+    full = bench.physics_run(x, v, L, 1.5, 10, rbl.RBL_FP32, True, 1, CFG, **ch)
+    rc25 = bench.physics_run(x, v, L, 2.5, 10, rbl.RBL_FP32, False, 1, CFG, **ch)
+    rc15 = bench.physics_run(x, v, L, 1.5, 10, rbl.RBL_FP32, False, 1, CFG, **ch)
+    return full, rc25, rc15
+
+
+def test_charged_fluid_matches_full_list_at_rc25(charged_runs):
+    full, rc25, _ = charged_runs
+    c = bench.physics_compare(rc25, full, CFG["dr"])
+    for k in ("P_bath", "U", "T"):
+        assert abs(c[k]["z"]) < 3.0, (k, c[k])
+    assert c["g"]["chi2_per_bin"] < 2.5, c["g"]
+
+
+def test_charged_fluid_heating_follows_estimator_variance(charged_runs):
+    full, _, rc15 = charged_runs
+    dT = rc15["T"][0] - full["T"][0]
+    pred = rc15["heating"]["dT_predicted"]
+    assert dT > 10 * (rc15["T"][1] + full["T"][1])
+    assert abs(dT - pred) < 0.3 * pred, (dT, pred)
