@@ -213,18 +213,19 @@ constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows rea
 // the charged fluid at N = 2^20, best block shape of each): shell sampling and the
 // full list, with or without the Ewald term, run fastest with 4 gathers in flight and
 // 64 registers (4 blocks of 256 threads per SM), the stencil pool with 12 and 80 (8
-// and 80 with the Ewald term).  The FP64 path needs up to 128 registers and runs at
-// the FP64 rate anyway.
-template <int MODE, bool EWALD>
+// and 80 with the Ewald term); the energy variants (last step of a call, one-step
+// calls) keep their energy and virial sums in 72.  The FP64 path needs up to 128
+// registers and runs at the FP64 rate anyway.
+template <int MODE, bool ENERGY, bool EWALD>
 struct ForceTuning {
     static constexpr int gather = MODE == 3 ? (EWALD ? 8 : 12) : 4;
-    static constexpr int regs = MODE == 3 ? 80 : 64;
+    static constexpr int regs = MODE == 3 ? 80 : (ENERGY ? 72 : 64);
 };
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>
-__global__ void __maxnreg__((FP32 ? ForceTuning<MODE, EWALD>::regs : 128)) k_force(View v, int step_offset)
+__global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128)) k_force(View v, int step_offset)
 {
-    constexpr int kGather = ForceTuning<MODE, EWALD>::gather;
+    constexpr int kGather = ForceTuning<MODE, ENERGY, EWALD>::gather;
     // staged mask words [kMaskStage][blockDim] and the set bits before each of them
     extern __shared__ unsigned s_dyn[];
     const int bd = blockDim.x;
