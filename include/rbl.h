@@ -212,9 +212,11 @@ rbl_status rbl_step_async(rbl_ctx *ctx, int n);
 rbl_status rbl_observables(rbl_ctx *ctx, rbl_obs *out);
 
 /* rbl_observables without the wait: enqueues on the context's stream the kinetic sums,
- * the assembly of the same rbl_obs[R] values on the device, and their copy into
- * out[R] (host memory, page-locked for the copy to be asynchronous, or device memory
- * with ptr_is_device = 1), and returns.  out is valid once the stream has reached the
+ * the assembly of the same rbl_obs[R] values on the device, and their delivery into
+ * out[R] (host memory, or device memory with ptr_is_device = 1), and returns.  Page-
+ * locked host memory and device memory are written by the assembling kernel itself;
+ * other host memory receives a copy, which is asynchronous only if that memory is
+ * page-locked.  out is valid once the stream has reached the
  * copy (synchronise the stream, or make any synchronising call).  Device flags are
  * not read here; the next synchronising call reports them.  For reading the scalars
  * every step without stalling the step sequence. */

@@ -784,10 +784,22 @@ rbl_status enqueue_observables(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
     rbl_status st = ensure_force(ctx, true);
     if (st != RBL_OK) return st;
     CK(launch_kinetic(ctx->view, ctx->stream));
+    // page-locked host memory (mapped into the device's address space) and device
+    // memory are written by the kernel itself; anything else through the staging area
+    void *direct = ptr_is_device ? (void *)out : nullptr;
+    if (!ptr_is_device) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+            direct = at.devicePointer;
+        cudaGetLastError(); // an unregistered pointer is not an error here
+    }
+    if (direct) {
+        CK(launch_obs(ctx->view, (rbl_obs *)direct, ctx->prm.r_s, ctx->stream));
+        return RBL_OK;
+    }
     rbl_obs *dev = (rbl_obs *)((char *)ctx->view.staging + obs_staging_offset(ctx->view.ntile));
     CK(launch_obs(ctx->view, dev, ctx->prm.r_s, ctx->stream));
-    CK(cudaMemcpyAsync(out, dev, sizeof(rbl_obs) * (size_t)ctx->R,
-                       ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(out, dev, sizeof(rbl_obs) * (size_t)ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
     return RBL_OK;
 }
 
