@@ -129,3 +129,28 @@ def test_ensemble_workload_matches_single_contexts():
         assert np.array_equal(xs[r], x1) and np.array_equal(vs[r], v1), r
         assert obs[r]["n_rebuild"] == s.observables()["n_rebuild"], r
     assert all(np.isfinite(o["T_kin"]) for o in obs)
+
+
+@pytest.mark.parametrize("precision", [rbl.RBL_FP64, rbl.RBL_FP32])
+def test_multi_chunk_replica_matches_single_context(precision):
+    """A replica with more than one chunk of 256 sixty-four-thread groups (N = 40,000:
+    3 chunks) beside small ones: its FP64 force sums (mean force) and energy sums go
+    through the two-stage reduction and must equal a standalone context's bit for bit."""
+    spec = [(900, 0.8, 1.2), (40000, 0.8, 1.5), (1500, 0.7, 1.0)]
+    reps = []
+    for r, (N, rho, T) in enumerate(spec):
+        x, L = inputs.fcc(N, rho, 0.2, seed=70 + r)
+        reps.append(rbl.Replica(x, inputs.maxwell_boltzmann(N, T, seed=70 + r), L, T, 70 + r))
+    ens = rbl.Ensemble(reps, precision=precision, **SHARED)
+    ens.step(12)
+    xs = ens.split(ens.get_state()[0])
+    F = ens.split(ens.forces())
+    obs = ens.observables()
+    for r, rp in enumerate(reps):
+        s = _single(rp, precision)
+        s.step(12)
+        assert np.array_equal(xs[r], s.get_state()[0]), r
+        assert np.array_equal(F[r], s.forces()), r
+        o = s.observables()
+        assert obs[r]["U_est"] == o["U_est"] and obs[r]["W_est"] == o["W_est"], r
+        assert obs[r]["K"] == o["K"], r
