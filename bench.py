@@ -869,12 +869,26 @@ def cpu_baseline(x, v, L, steps, steps_single=3, q=None, alpha=0.0):
     t1 = time.perf_counter()
     oracle.run(x, v, *args, steps_single, q=q, alpha=alpha)
     t1 = time.perf_counter() - t1
+    # the small parity system (N = 1000, rho* = 0.8, FP64 NVE, 100 steps), 1 thread and
+    # every core
+    from paper_2105_04884_gb300 import inputs
+
+    xs, Ls = inputs.fcc(1000, 0.8, 0.01, seed=1)
+    vs = inputs.maxwell_boltzmann(1000, 1.5, seed=1)
+    small = {}
+    for th in (1, cores):
+        oracle.set_threads(th)
+        t2 = time.perf_counter()
+        oracle.run(xs, vs, Ls, w["rc"], w["rs"], w["skin"], w["p"], w["dt"], 1.5, 0.0, 1, 100)
+        small[th] = 1000 * 100 / (time.perf_counter() - t2)
     oracle.set_threads(cores)
     return {"value": len(x) * steps / t, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{steps} steps of the same N={len(x)} workload from its start (includes the initial list "
                       f"build), FP64 C oracle with OpenMP on {cores} threads",
             "single_thread": {"value": len(x) * steps_single / t1, "unit": "particle-steps/s", "cores": 1,
-                              "sample": f"{steps_single} steps of the same workload from its start, 1 thread"}}
+                              "sample": f"{steps_single} steps of the same workload from its start, 1 thread"},
+            "parity_system_N1000": {"unit": "particle-steps/s", "single_thread": small[1], "all_cores": small[cores],
+                                    "sample": "100 FP64 velocity-Verlet steps of N = 1000, rho* = 0.8"}}
 
 
 REF_BUDGET_S = 120.0  # timed oracle work of the reference arm
