@@ -88,3 +88,26 @@ def test_single_rank_helpers():
     x1, _, L = bench.make_workload(2000, 1)
     x2, _, _ = bench.make_workload(2000, 2)
     assert x1.shape == (2000, 3) and not np.array_equal(x1, x2)
+
+
+def test_traffic_figure_only_for_matching_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu figure only while the force
+    kernel's and the list build's sources are the ones it was measured on."""
+    import json
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2105_04884_gb300 import _build
+
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    fig = {"dram_bytes_per_particle": 270.0, "source_sha": _build.force_digest()}
+    (prof / "force_kernel_traffic.json").write_text(json.dumps(fig))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic(1000) == pytest.approx(270.0 * 1000)
+    fig["source_sha"] = "0" * 16
+    (prof / "force_kernel_traffic.json").write_text(json.dumps(fig))
+    assert bench.load_traffic(1000) is None
+    # the measured peak, else the documented fallback
+    assert bench.load_peaks()[1] == "fallback" and bench.load_peaks()[0] == 6800.0
