@@ -303,9 +303,10 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int res
  * first call before any stream capture.  Systems whose workspace (as
  * rbl_workspace_size reports) exceeds 48 MiB are rejected with RBL_ENOMEM (about
  * 60,000 particles at rho* = 0.8 with the default radii); invalid parameters with
- * RBL_EINVAL, and so is RBL_POT_LJ_EWALD (this call takes no charges).  Every call shares the array, so calls that overlap on the GPU (two
- * streams, two host threads) race: serialise them.  Each call resets the parts it
- * reads; the array keeps the last call's contents otherwise. */
+ * RBL_EINVAL, and so is RBL_POT_LJ_EWALD (this call takes no charges).  Every call
+ * shares the array, so calls that overlap on the GPU (two streams, two host threads)
+ * race: serialise them.  Each call resets the parts it reads; the array keeps the
+ * last call's contents otherwise. */
 rbl_status rbl_forces_static(const rbl_params *prm, int N, const double *x, long long step, double *F, void *stream);
 
 /* Releases the handle (the workspace stays the caller's). NULL is ignored. */

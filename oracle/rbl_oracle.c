@@ -640,8 +640,9 @@ void orc_lj(int n, const double *r, double *u_out, double *fmag_out)
  * is the Floyd sample of row positions drawn from Philox stream 0 of (seed, step,
  * tag i).  Also returns this particle's halves of the energy and virial estimates. */
 static void force_one(int i, const double *x, const uint32_t *u, const fixed_frame *f, const thresholds *t,
-                      const pair_pot *pp, const double L[3], int p, uint64_t seed, uint64_t step, const int32_t *crow, int nc,
-                      const int32_t *srow, int ns, int32_t *pos, double Fi[3], double *e_i, double *w_i,
+                      const pair_pot *pp, const double L[3], int p, uint64_t seed, uint64_t step,
+                      const int32_t *crow, int nc, const int32_t *srow, int ns, int32_t *pos, double Fi[3],
+                      double *e_i, double *w_i,
                       int32_t *batch_out, int32_t *batch_n)
 {
     double fc[3] = {0, 0, 0}, fs[3] = {0, 0, 0};

@@ -461,7 +461,8 @@ rbl_status ensure_graph(rbl_ctx *ctx, int kind)
             cp.conditional.size = 1;
             ec = cudaGraphAddNode(&cond_node, g, deps, nullptr, ndeps, &cp);
         }
-        if (ec == cudaSuccess) ec = cudaStreamUpdateCaptureDependencies(s, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (ec == cudaSuccess)
+            ec = cudaStreamUpdateCaptureDependencies(s, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (ec == cudaSuccess) ec = launch_forces(ctx->view, 1, 1, last, s);
         if (ec == cudaSuccess && last) ec = launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, s);
         cudaGraph_t gout = nullptr;

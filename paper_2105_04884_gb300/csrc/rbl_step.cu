@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck, double 
             ws.init(b.seed, v.sc->step, (uint32_t)tag, 1u);
             float av[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) av[k] = __fmul_rn(__fadd_rn((float)(ws.next() >> 9), 0.5f), 1.1920928955078125e-7f);
+            for (int k = 0; k < 4; ++k)
+                av[k] = __fmul_rn(__fadd_rn((float)(ws.next() >> 9), 0.5f), 1.1920928955078125e-7f);
             float r0 = sqrtf(-2.0f * logf(av[0]));
             float r1 = sqrtf(-2.0f * logf(av[2]));
             float s1, c1v;
