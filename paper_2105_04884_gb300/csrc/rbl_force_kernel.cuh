@@ -208,6 +208,10 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 // rbl_autotune); the staging arrays are dynamic shared memory sized for the block.
 static_assert(kMinBlock == 64 && kMaxForceThreads % 64 == 0, "per-block partials are sized for kMinBlock");
 constexpr int kMaskStage = 32;  // mask words staged per thread (longer rows read directly)
+// the rank search halves its step from kMaskStage / 2, so it reaches every staged word
+// only for a power of two
+static_assert(kMaskStage > 0 && (kMaskStage & (kMaskStage - 1)) == 0 && kMaskStage <= 32,
+              "kMaskStage must be a power of two no larger than 32");
 
 // Gather width and FP32 register cap per mode, measured on GB300 (the LJ fluid and
 // the charged fluid at N = 2^20, best block shape of each): shell sampling and the
