@@ -39,6 +39,8 @@ def test_params_default_and_status_strings(lib):
     prm = rbl.rbl_params()
     lib.rbl_params_default(ctypes.byref(prm))
     assert prm.cells_per_cutoff == 2 and prm.subtract_net_force == 1 and prm.precision == rbl.RBL_FP32
+    assert prm.p == 10 and prm.dt == 0.005 and prm.sampling == rbl.RBL_SAMPLE_SHELL
+    assert prm.potential == rbl.RBL_POT_LJ and prm.alpha == 0.0 and prm.rho_cap == 0.0
     for code, name in rbl.STATUS.items():
         assert lib.rbl_status_string(code).decode() == name
 
@@ -122,3 +124,32 @@ def test_batch_validation(lib):
     assert lib.rbl_create_batch(None, 0, None, None, 0, None, ctypes.byref(h)) == 1
     lib.rbl_destroy(h)
     assert lib.rbl_replicas(None) == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """rbl_params and rbl_obs as the C compiler lays them out from include/rbl.h equal
+    the ctypes structures the binding passes (field offsets and total size)."""
+    import os
+    import subprocess
+
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rbl.h"', "int main(void) {"]
+    for st in (rbl.rbl_params, rbl.rbl_obs):
+        name = st.__name__
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["cc", "-I", inc, "-o", str(exe), str(src)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, value = line.split()
+        st = rbl.rbl_params if name == "rbl_params" else rbl.rbl_obs
+        expect = ctypes.sizeof(st) if field == "sizeof" else getattr(st, field).offset
+        assert int(value) == expect, (name, field, value, expect)
+        seen += 1
+    assert seen == 2 + len(rbl.rbl_params._fields_) + len(rbl.rbl_obs._fields_)
