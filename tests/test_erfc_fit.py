@@ -46,3 +46,20 @@ def test_relative_error_against_scipy():
     approx = (t32 * hp).astype(np.float32) * ex
     rel32 = np.abs(approx.astype(np.float64) / erfc(x32.astype(np.float64)) - 1.0)
     assert rel32[x <= 5.0].max() < 2e-6
+
+
+def test_header_is_the_generators_output():
+    """The committed coefficients are what csrc/erfc_fit.py computes (to binary32
+    rounding; the least-squares solve may differ in the last FP64 bits by platform)."""
+    pytest.importorskip("scipy.special")
+    import importlib.util
+
+    path = os.path.join(os.path.dirname(HDR), "erfc_fit.py")
+    spec = importlib.util.spec_from_file_location("erfc_fit", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    P, a = _coef()
+    c = mod.fit()
+    assert float(P) == pytest.approx(mod.P, rel=1e-7)
+    assert len(c) == len(a)
+    assert np.allclose(c.astype(np.float32), a, rtol=1e-6, atol=1e-8)
