@@ -172,11 +172,11 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def load_traffic(N):
+def load_traffic(N, name="force_kernel_traffic.json"):
     """DRAM bytes per launch of the force kernel from the committed ncu summary, if it
     was taken on the current force-kernel and list-build sources (else None).  The capture is of a smaller
     system; traffic grows in proportion to N, so it is scaled per particle."""
-    path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -703,7 +703,7 @@ def run_ours(a, rank, world, local):
     t_force = phase_ms[2] / nsteps * 1e-3
     achieved = alg_bytes_pp * N / t_force / 1e9
     peak, peak_kind = load_peaks()
-    traffic = None if ewald else load_traffic(N)
+    traffic = load_traffic(N, "force_kernel_traffic_ewald.json" if ewald else "force_kernel_traffic.json")
     result = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
