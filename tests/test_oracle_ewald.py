@@ -170,3 +170,19 @@ def test_charged_shell_estimator_unbiased(charged):
     live = var > 1e-12
     assert live.sum() > 1000
     assert np.quantile(z[live], 0.99) < 3.5 and z[live].max() < 6.0
+
+
+def test_charged_inputs():
+    """The seeded charge generators: neutral, half +q and half -q (one 0 for odd N), a
+    seed-dependent order; the rock-salt lattice has opposite charges on nearest neighbours."""
+    for N in (10, 11, 1000):
+        q = inputs.charges(N, 2.0, seed=4)
+        assert q.sum() == 0.0 and (q == 2.0).sum() == N // 2 and (q == -2.0).sum() == N // 2
+    assert not np.array_equal(inputs.charges(100, 1.0, seed=1), inputs.charges(100, 1.0, seed=2))
+    x, L, q = inputs.rock_salt(4, 1.1)
+    d = x[:, None, :] - x[None, :, :]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(-1))
+    nn = np.isclose(r, 1.1)
+    assert nn.sum() == 6 * len(x)  # six nearest neighbours each
+    assert np.all((q[:, None] * q[None, :])[nn] == -1.0)
