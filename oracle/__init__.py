@@ -5,9 +5,12 @@ the CPU-baseline leg of ``bench.py``; never by the library.  The arithmetic live
 ``rbl_oracle.c`` (plain C, compiled with ``-ffp-contract=off``); this module only
 builds it and marshals numpy arrays.  It shares nothing with the CUDA path.
 
-Parity status: every function here is pinned by ``tests/test_oracle_*.py`` except
-the BAOAB noise path over many steps, whose statistics are checked (<v^2> -> T)
-but whose individual trajectories have nothing independent to compare with.
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``.  The
+BAOAB step with friction is pinned step by step (the drift is the trapezoid of the
+velocities around the O step, with and without forces; the zero-temperature free
+flight has a closed form; the free-particle position variance is derived from the
+splitting); long noisy trajectories are checked statistically (<v^2> -> T), since
+their individual paths have nothing independent to compare with.
 """
 from __future__ import annotations
 

@@ -149,3 +149,91 @@ def test_density_profile_counts():
     vapour = np.abs(z - L[2] / 2) > 0.3 * L[2]
     assert abs(rho[liquid].mean() - 0.75) < 0.02
     assert rho[vapour].mean() < 0.05
+
+
+# ---------------------------------------------------------------------------
+# BAOAB positions with friction (gamma > 0).  One step of the splitting is
+# B: v += dt/2 F; A: x += dt/2 v; O: v = c1 v + c2 xi; A: x += dt/2 v; B: v += dt/2 F
+# (Leimkuhler & Matthews; the underdamped Langevin equation, Eq. (2)).  The pins
+# below follow from that sequence alone and fail for a dropped or doubled half
+# drift, a single full-dt drift, or an O step outside the two A steps.
+# ---------------------------------------------------------------------------
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def test_baoab_free_particles_zero_temperature_closed_form():
+    """T = 0, no pair inside r_s: v_n = c1^n v0 and
+    x_n = x0 + (dt/2)(1 + c1) v0 (1 - c1^n) / (1 - c1)."""
+    x, L = _sparse_lattice(4, 9.0)
+    v0 = np.random.default_rng(5).normal(size=x.shape)
+    gamma, dt, n = 1.3, 0.01, 37
+    x2, v2, F, _ = oracle.run(x, v0, L, 1.5, 3.5, 0.3, 10, dt, 0.0, gamma, 2, n, subtract_mean=False)
+    assert np.all(F == 0.0)
+    c1 = math.exp(-gamma * dt)
+    assert np.abs(v2 - c1**n * v0).max() < 1e-13
+    want = x + 0.5 * dt * (1.0 + c1) * v0 * (1.0 - c1**n) / (1.0 - c1)
+    assert np.abs(_min_image(x2 - want, L)).max() < 1e-12
+    # the alternatives differ from it by far more than the tolerance
+    for wrong in (0.5 * dt * c1, 0.5 * dt, dt, dt * c1):
+        alt = x + wrong * v0 * (1.0 - c1**n) / (1.0 - c1)
+        assert np.abs(_min_image(x2 - alt, L)).max() > 1e-4
+
+
+def test_baoab_free_particles_trapezoid_drift_with_noise():
+    """T > 0, free particles, one step per call: the two half drifts straddle the
+    O step, so x_{k+1} - x_k = (dt/2)(v_k + v_{k+1}) for every particle, whatever
+    the noise drew; the noise itself changes v (v_{k+1} != c1 v_k)."""
+    x, L = _sparse_lattice(8, 9.0)
+    v = inputs.maxwell_boltzmann(len(x), 1.2, seed=6)
+    gamma, dt, T = 1.0, 0.005, 1.7
+    c1 = math.exp(-gamma * dt)
+    for k in range(6):
+        x2, v2, _, _ = oracle.run(x, v, L, 1.5, 3.5, 0.3, 10, dt, T, gamma, 4, 1, step0=k, subtract_mean=False)
+        d = _min_image(x2 - x, L)
+        # two drifts, each rounded at the position's magnitude (up to L)
+        assert np.abs(d - 0.5 * dt * (v + v2)).max() < 8 * np.spacing(L.max())
+        assert np.abs(v2 - c1 * v).max() > 1e-3
+        x, v = x2, v2
+
+
+def test_baoab_free_particles_position_variance():
+    """T > 0, v0 = 0, n steps: x_n - x0 = sum_m a_m xi_m with
+    a_m = (dt/2) c2 [1 + (1 + c1)(1 - c1^(n-1-m)) / (1 - c1)], c2 = sqrt((1 - c1^2) T),
+    so each component has variance sum_m a_m^2 (derived from the splitting)."""
+    x, L = _sparse_lattice(16, 9.0)
+    gamma, dt, T, n = 2.0, 0.05, 1.5, 4
+    c1 = math.exp(-gamma * dt)
+    c2 = math.sqrt((1 - c1 * c1) * T)
+    a = [0.5 * dt * c2 * (1 + (1 + c1) * (1 - c1 ** (n - 1 - m)) / (1 - c1)) for m in range(n)]
+    var = sum(t * t for t in a)
+    x2, _, _, _ = oracle.run(x, np.zeros_like(x), L, 1.5, 3.5, 0.3, 10, dt, T, gamma, 7, n, subtract_mean=False)
+    d = _min_image(x2 - x, L).ravel()
+    m = d.size
+    assert abs(d.mean()) < 5 * math.sqrt(var / m)
+    assert abs(d.var() / var - 1) < 5 * math.sqrt(2 / m)
+    # an O step before both drifts (x += dt v after O) would give sum of (dt c2 ...)^2
+    alt = sum((dt * c2 * (1 - c1 ** (n - m)) / (1 - c1)) ** 2 for m in range(n))
+    assert abs(alt / var - 1) > 10 * math.sqrt(2 / m)
+
+
+def test_baoab_drift_with_forces():
+    """Interacting LJ fluid, gamma > 0, one step per call: the drift uses the
+    velocity after the opening half kick and after the O step, so
+    x_{k+1} - x_k = (dt/2)[v_k + v_{k+1} + (dt/2)(F_k - F_{k+1})], F_k the force the
+    step opens with (a call of zero steps at the same state and step returns it:
+    each call builds its lists at its start) and F_{k+1} the one it closes with."""
+    x, L = inputs.fcc(500, 0.8, 0.05, seed=8)
+    v = inputs.maxwell_boltzmann(500, 1.5, seed=8)
+    dt, T, gamma = 0.005, 1.5, 1.0
+    for k in range(5):
+        _, _, F, _ = oracle.run(x, v, L, 1.5, 3.5, 0.3, 10, dt, T, gamma, 3, 0, step0=k)
+        assert np.abs(F).max() > 1.0
+        x2, v2, F2, _ = oracle.run(x, v, L, 1.5, 3.5, 0.3, 10, dt, T, gamma, 3, 1, step0=k)
+        d = _min_image(x2 - x, L)
+        want = 0.5 * dt * (v + v2 + 0.5 * dt * (F - F2))
+        assert np.abs(d - want).max() < 8 * np.spacing(L.max())
+        # a drift from the kicked velocity alone (O after both drifts) is far off
+        alt = 0.5 * dt * (2 * v + dt * F)
+        assert np.abs(d - alt).max() > 1e-5
+        x, v = x2, v2
