@@ -60,7 +60,9 @@ typedef enum {
     RBL_EINVAL = 1,      /* bad argument (message in rbl_last_error) */
     RBL_ENOMEM = 2,      /* workspace too small */
     RBL_EOVERFLOW = 3,   /* a list row or cell exceeded its capacity; recreate with larger caps */
-    RBL_ENONFINITE = 4,  /* a non-finite position, velocity or force was produced */
+    RBL_ENONFINITE = 4,  /* a non-finite position, velocity or force was produced, a force left the
+                            fixed-point range (|F| >= 2^29: overlapping particles), or a particle moved
+                            more than a box length in one step */
     RBL_ETIMEOUT = 5,    /* a bounded device wait gave up */
     RBL_ECUDA = 6        /* a CUDA runtime call failed (message in rbl_last_error) */
 } rbl_status;
@@ -183,6 +185,23 @@ rbl_status rbl_set_charges(rbl_ctx *ctx, const double *q);
  * step counter (may be NULL). */
 rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, int ptr_is_device);
 
+/* Checkpoint and resume (Algorithm 1: each step's batches are keyed by (seed, step,
+ * tag) and drawn from the rows of the last list build, so a resumed run needs those
+ * rows, not a fresh build).  A checkpoint holds the positions and velocities (tag
+ * order), the fixed-point images the lists were last built from, the step counter
+ * and each replica's rebuild count: rbl_checkpoint_size() bytes, an opaque byte
+ * buffer (host or device memory, 8-byte aligned).  rbl_load_checkpoint into a
+ * context created with the same parameters and sizes rebuilds the lists from the
+ * saved images and recomputes the force at the saved step when it is next needed,
+ * so the steps that follow are bit-identical to continuing the saved context (every
+ * replica, either precision); it needs no extra rebuild at the resume step.  Charges
+ * (RBL_POT_LJ_EWALD) are not part of a checkpoint: set them with rbl_set_charges,
+ * before or after loading.  RBL_EINVAL for a buffer that is not a checkpoint or that
+ * was saved from a context of other sizes or precision.  Both calls synchronise. */
+rbl_status rbl_checkpoint_size(const rbl_ctx *ctx, size_t *bytes);
+rbl_status rbl_save_checkpoint(rbl_ctx *ctx, void *buf, int ptr_is_device);
+rbl_status rbl_load_checkpoint(rbl_ctx *ctx, const void *buf, int ptr_is_device);
+
 /* Builds the cell list and the two-level neighbour lists from the current positions
  * (Sec. 2: linked cells, core list r < r_c + skin, shell list
  * max(r_c - skin, 0) <= r < r_s + skin; or the full list r < r_s + skin).
@@ -280,12 +299,13 @@ rbl_status rbl_autotune(rbl_ctx *ctx, int trials, int *force_threads, int *build
 
 /* Phase timing.  While enabled, rbl_step launches each step's phases directly (no
  * graph replay) and brackets them with CUDA events on the context's stream:
- * phase 0 = kick/drift/thermostat kernel, 1 = rebuild chain (device-conditional:
- * near-empty when no rebuild is due), 2 = force kernel alone, 3 = force reduction.
- * rbl_phase_times adds the elapsed milliseconds of every timed step since the last
- * reset to ms[4] and reports the number of timed steps; reset = 1 clears them. */
+ * phase 0 = kick/drift/thermostat kernel, 1 = cell hash, scan, sort and permutation,
+ * 2 = list build (1 and 2 are device-conditional: their kernels return at once when
+ * no rebuild is due), 3 = force kernel alone, 4 = force reduction.  rbl_phase_times
+ * writes the elapsed milliseconds of every timed step since the last reset, summed
+ * per phase, to ms[5] and reports the number of timed steps; reset = 1 clears them. */
 rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable);
-rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int reset);
+rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[5], long long *steps, int reset);
 
 /* Allocation-free force evaluation (the paper has no counterpart; this is a service
  * for callers that may not allocate).  Some callers cannot allocate device memory
@@ -299,8 +319,9 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int res
  * nothing: its working memory is one file-scope device array of 48 MiB, which every
  * device where the library's module is loaded (at the latest on the first call of
  * this function there) holds until the process exits.  The first call on a device,
- * made with that device current, looks up the array's device address; make that
- * first call before any stream capture.  Systems whose workspace (as
+ * made with that device current, sets the array up there and looks up its device
+ * address; make that first call before any stream capture.  Later calls look the
+ * address up again (a device reset may move it).  Systems whose workspace (as
  * rbl_workspace_size reports) exceeds 48 MiB are rejected with RBL_ENOMEM (about
  * 60,000 particles at rho* = 0.8 with the default radii); invalid parameters with
  * RBL_EINVAL, and so is RBL_POT_LJ_EWALD (this call takes no charges).  Every call

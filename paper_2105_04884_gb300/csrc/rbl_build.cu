@@ -505,7 +505,7 @@ __global__ void k_finish_all(View v) { v.sc->rebuild = 0; }
 
 } // namespace
 
-cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s)
+cudaError_t launch_rebuild_sort(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s)
 {
     int cond = conditional ? 1 : 0;
     int gN = ceil_div(v.N, kBlock);
@@ -520,6 +520,12 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_sort_cells<<<gC, kBlock, 0, s>>>(v, cond);
     k_permute<<<gN, kBlock, 0, s>>>(v, cond);
     k_copy_back<<<gN, kBlock, 0, s>>>(v, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild_lists(const View &v, bool conditional, cudaStream_t s)
+{
+    int cond = conditional ? 1 : 0;
     const dim3 gB(ceil_div(v.ncell, v.build_warps)), bB(v.build_warps * 32);
     if (v.sampling) k_build_lists<kListPool><<<gB, bB, 0, s>>>(v, cond);
     else if (v.full_list) k_build_lists<kListFull><<<gB, bB, 0, s>>>(v, cond);
@@ -527,6 +533,13 @@ cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, c
     k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
     k_finish_all<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s)
+{
+    cudaError_t e = launch_rebuild_sort(v, n_scan_blocks, conditional, s);
+    if (e == cudaSuccess) e = launch_rebuild_lists(v, conditional, s);
+    return e;
 }
 
 cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHandle h, cudaStream_t s)

@@ -180,7 +180,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.pchunks = (int)((max_slots / kMinBlock + kChunkGroups - 1) / kChunkGroups);
     const size_t Nz = (size_t)P.N;
     const size_t Nq = p->potential == RBL_POT_LJ_EWALD ? Nz : 0; // charges only with the Ewald term
-    size_t st = 48 * (size_t)n_real;                   // packed x and v (host copies)
+    size_t st = 64 * (size_t)n_real + 4096;            // packed x, v and images (host copies, checkpoints)
     if (st < 4 * Nz * (size_t)(p->p + 1)) st = 4 * Nz * (size_t)(p->p + 1); // batch hook
     if (st < obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R)       // kinetic partials, then rbl_obs[R]
         st = obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R;
@@ -347,6 +347,12 @@ rbl_status check_flags(rbl_ctx *ctx, bool replicas = false)
     rbl_status st = read_scalars(ctx, replicas);
     if (st != RBL_OK) return st;
     unsigned f = ctx->h_sc->flags;
+    // a blow-up first: row or cell overflows can follow from it
+    if (f & kFlagNonFinite) {
+        set_err(ctx, "non-finite position, velocity or force, a force beyond the fixed-point range (overlapping "
+                     "particles), or a particle that moved more than a box length in one step");
+        return RBL_ENONFINITE;
+    }
     if (f & (kFlagOverflow | kFlagCellOverflow)) {
         if (!replicas) read_scalars(ctx, true);
         int nc = 0, m = 0;
@@ -357,10 +363,6 @@ rbl_status check_flags(rbl_ctx *ctx, bool replicas = false)
         set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest stencil population %d / cap %d)", nc,
                 ctx->view.cap_c, m, ctx->view.Mcap);
         return RBL_EOVERFLOW;
-    }
-    if (f & kFlagNonFinite) {
-        set_err(ctx, "non-finite position or velocity");
-        return RBL_ENONFINITE;
     }
     if (f & kFlagRngLimit) {
         set_err(ctx, "bounded-draw rejection limit reached");
@@ -389,20 +391,26 @@ rbl_status ensure_force(rbl_ctx *ctx, bool energy)
     return RBL_OK;
 }
 
+// Phases of a timed step: kick/drift/thermostat, cell sort chain, list build,
+// force kernel, force reduction.
+constexpr int kPhases = 5, kPhaseEvents = kPhases + 1;
+
 // One steady-state step: kick(ck)+drift+O, conditional rebuild, force at n+1.
-// ev (optional): 5 events recorded at the phase boundaries.
+// ev (optional): kPhaseEvents events recorded at the phase boundaries.
 cudaError_t enqueue_step(rbl_ctx *ctx, double ck, bool energy, cudaEvent_t *ev = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (ev) e = cudaEventRecord(ev[0], ctx->stream);
     if (e == cudaSuccess) e = launch_integrate(ctx->view, ck, true, ctx->stream);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], ctx->stream);
-    if (e == cudaSuccess) e = launch_rebuild(ctx->view, ctx->n_scan_blocks, true, ctx->stream);
+    if (e == cudaSuccess) e = launch_rebuild_sort(ctx->view, ctx->n_scan_blocks, true, ctx->stream);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], ctx->stream);
-    if (e == cudaSuccess) e = launch_force_kernel(ctx->view, 1, energy, ctx->stream);
+    if (e == cudaSuccess) e = launch_rebuild_lists(ctx->view, true, ctx->stream);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], ctx->stream);
-    if (e == cudaSuccess) e = launch_force_finish(ctx->view, 1, energy, ctx->stream);
+    if (e == cudaSuccess) e = launch_force_kernel(ctx->view, 1, energy, ctx->stream);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], ctx->stream);
+    if (e == cudaSuccess) e = launch_force_finish(ctx->view, 1, energy, ctx->stream);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], ctx->stream);
     return e;
 }
 
@@ -410,10 +418,10 @@ rbl_status ensure_events(rbl_ctx *ctx, int steps)
 {
     if (ctx->ev_cap >= steps) return RBL_OK;
     int cap = steps < 64 ? 64 : steps;
-    cudaEvent_t *ev = (cudaEvent_t *)std::calloc((size_t)cap * 5, sizeof(cudaEvent_t));
+    cudaEvent_t *ev = (cudaEvent_t *)std::calloc((size_t)cap * kPhaseEvents, sizeof(cudaEvent_t));
     if (!ev) return RBL_ENOMEM;
-    for (int k = 0; k < ctx->ev_cap * 5; ++k) ev[k] = ctx->ev[k];
-    for (int k = ctx->ev_cap * 5; k < cap * 5; ++k) CK(cudaEventCreate(&ev[k]));
+    for (int k = 0; k < ctx->ev_cap * kPhaseEvents; ++k) ev[k] = ctx->ev[k];
+    for (int k = ctx->ev_cap * kPhaseEvents; k < cap * kPhaseEvents; ++k) CK(cudaEventCreate(&ev[k]));
     std::free(ctx->ev);
     ctx->ev = ev;
     ctx->ev_cap = cap;
@@ -690,6 +698,119 @@ rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, in
     return RBL_OK;
 }
 
+// Checkpoint buffer: header | n_rebuild[R] | x[n][3] | v[n][3] (doubles) | images[n][3]
+// (uint32), n = every replica's particles, tag order packed over replicas.
+struct CkptHeader {
+    char magic[8];          // "RBLCKPT1"
+    long long n_real;
+    long long step;
+    int R;
+    int precision;
+    int lists_valid;        // the lists were built from the saved images
+    int reserved[3];
+};
+
+static size_t ckpt_head_bytes(int R) { return (sizeof(CkptHeader) + 8 * (size_t)R + 15) & ~(size_t)15; }
+
+rbl_status rbl_checkpoint_size(const rbl_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return RBL_EINVAL;
+    *bytes = ckpt_head_bytes(ctx->R) + 60 * (size_t)ctx->n_real;
+    return RBL_OK;
+}
+
+rbl_status rbl_save_checkpoint(rbl_ctx *ctx, void *buf, int ptr_is_device)
+{
+    if (!ctx || !buf) return RBL_EINVAL;
+    rbl_status st = read_scalars(ctx, true);
+    if (st != RBL_OK) return st;
+    const size_t head = ckpt_head_bytes(ctx->R), n = (size_t)ctx->n_real;
+    std::vector<char> h(head, 0);
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "RBLCKPT1", 8);
+    hd.n_real = ctx->n_real;
+    hd.step = ctx->step;
+    hd.R = ctx->R;
+    hd.precision = ctx->prm.precision;
+    hd.lists_valid = ctx->lists_valid;
+    std::memcpy(h.data(), &hd, sizeof(hd));
+    for (int r = 0; r < ctx->R; ++r)
+        std::memcpy(h.data() + sizeof(CkptHeader) + 8 * (size_t)r, &ctx->h_rs[r].n_rebuild, 8);
+    char *dst = ptr_is_device ? (char *)buf : (char *)ctx->view.staging;
+    double *x = (double *)(dst + head);
+    unsigned *img = (unsigned *)(x + 6 * n);
+    CK(launch_store_state(ctx->view, x, x + 3 * n, ctx->stream));
+    CK(launch_store_images(ctx->view, img, ctx->stream));
+    if (ptr_is_device) {
+        CK(cudaMemcpyAsync(buf, h.data(), head, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return RBL_OK;
+    }
+    std::memcpy(buf, h.data(), head);
+    CK(cudaMemcpyAsync((char *)buf + head, dst + head, 60 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RBL_OK;
+}
+
+rbl_status rbl_load_checkpoint(rbl_ctx *ctx, const void *buf, int ptr_is_device)
+{
+    if (!ctx || !buf) return RBL_EINVAL;
+    const size_t head = ckpt_head_bytes(ctx->R), n = (size_t)ctx->n_real;
+    std::vector<char> h(head, 0);
+    if (ptr_is_device) {
+        CK(cudaMemcpyAsync(h.data(), buf, head, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::memcpy(h.data(), buf, head);
+    }
+    CkptHeader hd;
+    std::memcpy(&hd, h.data(), sizeof(hd));
+    if (std::memcmp(hd.magic, "RBLCKPT1", 8) != 0) {
+        set_err(ctx, "not an rbl checkpoint");
+        return RBL_EINVAL;
+    }
+    if (hd.n_real != ctx->n_real || hd.R != ctx->R || hd.precision != ctx->prm.precision || hd.step < 0) {
+        set_err(ctx, "checkpoint of %lld particles in %d replicas (precision %d) does not fit this context (%lld in %d, %d)",
+                hd.n_real, hd.R, hd.precision, ctx->n_real, ctx->R, ctx->prm.precision);
+        return RBL_EINVAL;
+    }
+    const char *src = (const char *)buf;
+    if (!ptr_is_device) {
+        CK(cudaMemcpyAsync(ctx->view.staging, src + head, 60 * n, cudaMemcpyHostToDevice, ctx->stream));
+        src = (const char *)ctx->view.staging - head;
+    }
+    const double *x = (const double *)(src + head);
+    const unsigned *img = (const unsigned *)(x + 6 * n);
+    DevScalars z{};
+    *ctx->h_sc = z;
+    ctx->h_sc->step = (unsigned long long)hd.step;
+    CK(cudaMemcpyAsync(ctx->view.sc, ctx->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->view.rs, 0, sizeof(RepScalars) * (size_t)ctx->R, ctx->stream));
+    CK(launch_load_state(ctx->view, x, x + 3 * n, ctx->stream));
+    CK(launch_load_images(ctx->view, img, ctx->stream));
+    if (hd.lists_valid) {
+        // the lists of the saved context: the rebuild chain run on the saved build
+        // images (in place of the current ones) puts the particles in that build's
+        // cell order and rebuilds its rows; then the current images are recomputed
+        // from the (permuted) positions
+        View vb = ctx->view;
+        vb.pos = vb.ubuild;
+        CK(launch_rebuild(vb, ctx->n_scan_blocks, false, ctx->stream));
+        CK(launch_requantize(ctx->view, ctx->stream));
+    }
+    rbl_status st = read_scalars(ctx, true);
+    if (st != RBL_OK) return st;
+    for (int r = 0; r < ctx->R; ++r)
+        std::memcpy(&ctx->h_rs[r].n_rebuild, h.data() + sizeof(CkptHeader) + 8 * (size_t)r, 8);
+    CK(cudaMemcpyAsync(ctx->view.rs, ctx->h_rs, sizeof(RepScalars) * (size_t)ctx->R, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->step = hd.step;
+    ctx->lists_valid = hd.lists_valid ? 1 : 0;
+    ctx->force_valid = 0;
+    ctx->energy_valid = 0;
+    return check_flags(ctx);
+}
+
 rbl_status rbl_build_lists(rbl_ctx *ctx)
 {
     if (!ctx) return RBL_EINVAL;
@@ -732,13 +853,13 @@ static rbl_status step_impl(rbl_ctx *ctx, int n, bool sync)
         st = ensure_events(ctx, n);
         if (st != RBL_OK) return st;
         for (int k = 0; k < n; ++k)
-            CK(enqueue_step(ctx, k == 0 ? 0.5 * ctx->prm.dt : ctx->prm.dt, k == n - 1, ctx->ev + 5 * k));
+            CK(enqueue_step(ctx, k == 0 ? 0.5 * ctx->prm.dt : ctx->prm.dt, k == n - 1, ctx->ev + kPhaseEvents * k));
         CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         for (int k = 0; k < n; ++k)
-            for (int ph = 0; ph < 4; ++ph) {
+            for (int ph = 0; ph < kPhases; ++ph) {
                 float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, ctx->ev[5 * k + ph], ctx->ev[5 * k + ph + 1]));
+                CK(cudaEventElapsedTime(&ms, ctx->ev[kPhaseEvents * k + ph], ctx->ev[kPhaseEvents * k + ph + 1]));
                 ctx->phase_ms[ph] += ms;
             }
         ctx->phase_steps += n;
@@ -1132,14 +1253,14 @@ rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable)
     return RBL_OK;
 }
 
-rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[4], long long *steps, int reset)
+rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[5], long long *steps, int reset)
 {
     if (!ctx) return RBL_EINVAL;
     if (ms)
-        for (int k = 0; k < 4; ++k) ms[k] = ctx->phase_ms[k];
+        for (int k = 0; k < kPhases; ++k) ms[k] = ctx->phase_ms[k];
     if (steps) *steps = ctx->phase_steps;
     if (reset) {
-        for (int k = 0; k < 4; ++k) ctx->phase_ms[k] = 0.0;
+        for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = 0.0;
         ctx->phase_steps = 0;
     }
     return RBL_OK;
@@ -1149,7 +1270,7 @@ void rbl_destroy(rbl_ctx *ctx)
 {
     if (!ctx) return;
     drop_graphs(ctx);
-    for (int k = 0; k < ctx->ev_cap * 5; ++k) cudaEventDestroy(ctx->ev[k]);
+    for (int k = 0; k < ctx->ev_cap * kPhaseEvents; ++k) cudaEventDestroy(ctx->ev[k]);
     std::free(ctx->ev);
     delete ctx->h_sc;
     delete[] ctx->h_rs;
@@ -1198,20 +1319,23 @@ std::mutex g_static_mutex;
 void *g_static_ptr[kMaxDevices]; // device address of g_static_scratch, per device ordinal
 
 // Device address of the scratch array on the current device.  The host-side name
-// g_static_scratch is only a stand-in; the address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// g_static_scratch is only a stand-in; the address comes from cudaGetSymbolAddress
+// with that device current.  The first call on a device sets it up (loading the
+// module there); it is looked up again on every call, so a device reset that reloads
+// the module (and may move the array) leaves no stale address behind.
 rbl_status static_scratch_address(void **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return RBL_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return RBL_EINVAL;
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return RBL_ECUDA;
-        g_static_ptr[dev] = p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return RBL_ECUDA;
     }
-    *out = g_static_ptr[dev];
+    g_static_ptr[dev] = p;
+    *out = p;
     return RBL_OK;
 }
 } // namespace

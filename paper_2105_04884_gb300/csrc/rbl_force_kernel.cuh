@@ -492,6 +492,10 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
             float f[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) f[a] = __fmaf_rn(s32, acc.f32[1][a], acc.f32[0][a]);
+            // a NaN or a force beyond the fixed-point range (overlapping particles)
+            // would be clamped by the conversion: report it instead
+            if (!(fabsf(f[0]) < kFixedRange) || !(fabsf(f[1]) < kFixedRange) || !(fabsf(f[2]) < kFixedRange))
+                atomicOr(&v.sc->flags, kFlagNonFinite);
             fx.add(f[0], f[1], f[2], fmaxf(fabsf(f[0]), fmaxf(fabsf(f[1]), fabsf(f[2]))));
 #pragma unroll
             for (int a = 0; a < 3; ++a) {

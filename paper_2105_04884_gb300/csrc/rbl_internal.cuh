@@ -28,7 +28,11 @@ static_assert(kBlock == kTile, "a per-particle block covers exactly one tile");
 constexpr int kMaxSeg = kMaxStencil * kMaxStencil;
 
 // Device flags (bit positions in DevScalars::flags).
+// kFlagNonFinite: a non-finite position, velocity or force, a binary32 force beyond
+// the fixed-point range (|F| >= 2^29, overlapping particles), or a particle that left
+// the box in one step (moved more than a box length).
 enum : unsigned { kFlagOverflow = 1u, kFlagNonFinite = 2u, kFlagCellOverflow = 4u, kFlagRngLimit = 8u };
+constexpr float kFixedRange = 536870880.0f; // below 2^29: |4 F| stays inside the int32 split of FixedAcc
 
 // Context-wide scalars living in device memory (one instance in the workspace).
 struct DevScalars {
@@ -558,6 +562,14 @@ __device__ __forceinline__ double wrap(double x, double L)
     return x;
 }
 
+// 0 <= x < L for finite x and L > 0, from the IEEE bit patterns: a negative x has
+// the sign bit set (a negative int64), and for x >= 0 the patterns order as the values.
+__device__ __forceinline__ bool in_box_bits(double x, double L)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 && b < __double_as_longlong(L);
+}
+
 // Not NaN/inf, from the exponent bits.
 __device__ __forceinline__ bool finite_bits(double x)
 {
@@ -583,9 +595,9 @@ struct rbl_ctx {
     size_t staging_bytes;
     cudaGraphExec_t graph_exec[4]; // captured steps: middle, first, last, single (enum StepGraph)
     int phase_timing;           // rbl_set_phase_timing
-    cudaEvent_t *ev;            // 5 events per timed step
+    cudaEvent_t *ev;            // kPhaseEvents events per timed step
     int ev_cap;                 // steps the event pool covers
-    double phase_ms[4];
+    double phase_ms[5];
     long long phase_steps;
     char err[512];
     rbl::DevScalars *h_sc;      // host mirror of the device scalars
@@ -599,7 +611,13 @@ struct rbl_ctx {
 namespace rbl {
 cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s);
 cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s);
+cudaError_t launch_store_images(const View &v, unsigned *img, cudaStream_t s);
+cudaError_t launch_load_images(const View &v, const unsigned *img, cudaStream_t s);
+cudaError_t launch_requantize(const View &v, cudaStream_t s);
 cudaError_t launch_rebuild(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s);
+// the two halves of launch_rebuild: cell hash, scan, sort and permutation; then the lists
+cudaError_t launch_rebuild_sort(const View &v, int n_scan_blocks, bool conditional, cudaStream_t s);
+cudaError_t launch_rebuild_lists(const View &v, bool conditional, cudaStream_t s);
 cudaError_t launch_set_rebuild_condition(const View &v, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_forces(const View &v, int step_offset, int advance, bool energy, cudaStream_t s);
 // prepare = true: set the kernel's attributes for a later captured launch, launch nothing

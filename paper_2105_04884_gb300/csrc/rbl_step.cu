@@ -102,6 +102,50 @@ __global__ void k_store(View v, double *x, double *vel)
     }
 }
 
+// Checkpoint I/O, tag order packed over replicas: the images of the last build,
+// out of cell order (k_store_images) and into load order, slot first + t for tag t
+// (k_load_images, after k_load).
+__global__ void k_store_images(View v, unsigned *img)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
+    const size_t t = (size_t)v.box[r].in0 + (size_t)v.tag[i];
+    const int4 u = v.ubuild[i];
+    img[t * 3 + 0] = (unsigned)u.x;
+    img[t * 3 + 1] = (unsigned)u.y;
+    img[t * 3 + 2] = (unsigned)u.z;
+}
+
+__global__ void k_load_images(View v, const unsigned *img)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
+    const Box &b = v.box[r];
+    const int t = i - b.first;
+    const size_t row = (size_t)b.in0 + (size_t)t;
+    v.ubuild[i] = make_int4((int)img[row * 3 + 0], (int)img[row * 3 + 1], (int)img[row * 3 + 2], t);
+}
+
+// The current fixed-point images from the FP64 positions (slot order as it stands).
+__global__ void k_requantize(View v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    bool live;
+    const int r = slot_replica(v, i, live);
+    if (!live) return;
+    const Box &b = v.box[r];
+    const size_t N = (size_t)v.N;
+    v.pos[i] = make_int4((int)quantize(v.x[i], b.inv[0]), (int)quantize(v.x[N + i], b.inv[1]),
+                         (int)quantize(v.x[2 * N + i], b.inv[2]), v.tag[i]);
+}
+
 // ck: kick coefficient (dt/2 or dt); cks = ck 2^-24, the kick per fixed-point unit
 // of force.  DRIFT = false: kick only (closing half-kick).
 //
@@ -168,7 +212,8 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck, double 
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double xa = wrap(xx[a], b.L[a]);
-            bad |= !finite_bits(xa) || !finite_bits(vv[a]);
+            // non-finite, or still outside the box: a step of more than a box length
+            bad |= !finite_bits(xa) || !finite_bits(vv[a]) || !in_box_bits(xa, b.L[a]);
             v.x[a * N + i] = xa;
             v.v[a * N + i] = vv[a];
             u[a] = quantize(xa, b.inv[a]);
@@ -303,6 +348,24 @@ cudaError_t launch_load_state(const View &v, const double *x, const double *vel,
 cudaError_t launch_set_charges(const View &v, const double *q_packed, cudaStream_t s)
 {
     k_set_charges<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, q_packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_images(const View &v, unsigned *img, cudaStream_t s)
+{
+    k_store_images<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_images(const View &v, const unsigned *img, cudaStream_t s)
+{
+    k_load_images<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_requantize(const View &v, cudaStream_t s)
+{
+    k_requantize<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v);
     return cudaGetLastError();
 }
 

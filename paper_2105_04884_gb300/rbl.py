@@ -64,7 +64,8 @@ EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch
            "rbl_build_lists", "rbl_forces", "rbl_step", "rbl_step_async", "rbl_observables",
            "rbl_observables_async", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows", "rbl_get_batch",
            "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config", "rbl_autotune", "rbl_set_phase_timing",
-           "rbl_phase_times", "rbl_forces_static", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
+           "rbl_phase_times", "rbl_forces_static", "rbl_checkpoint_size", "rbl_save_checkpoint",
+           "rbl_load_checkpoint", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
 
 _lib = None
 
@@ -112,6 +113,9 @@ def load(build_if_missing: bool = False):
     L.rbl_set_phase_timing.argtypes = [P, I]
     L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
     L.rbl_forces_static.argtypes = [ctypes.POINTER(rbl_params), I, P, LL, P, P]
+    L.rbl_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.rbl_save_checkpoint.argtypes = [P, P, I]
+    L.rbl_load_checkpoint.argtypes = [P, P, I]
     L.rbl_destroy.argtypes = [P]
     L.rbl_destroy.restype = None
     L.rbl_last_error.argtypes = [P]
@@ -243,6 +247,27 @@ class _Context:
     def build_lists(self):
         self._check(self.lib.rbl_build_lists(self.h))
 
+    def save_checkpoint(self, device=False):
+        """The context's checkpoint (state, build-time images, step, rebuild counts) as a
+        uint8 numpy array, or a uint8 tensor on the context's device."""
+        n = ctypes.c_size_t()
+        self._check(self.lib.rbl_checkpoint_size(self.h, ctypes.byref(n)))
+        if device:
+            buf = self._torch.empty(n.value, dtype=self._torch.uint8, device=self.device)
+        else:
+            buf = np.empty(n.value, np.uint8)
+        self._check(self.lib.rbl_save_checkpoint(self.h, _ptr(buf), int(device)))
+        return buf
+
+    def load_checkpoint(self, buf):
+        """Restore a checkpoint saved by a context of the same parameters and sizes."""
+        dev = self._is_dev(buf)
+        if dev:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+        else:
+            buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.rbl_load_checkpoint(self.h, _ptr(buf), int(dev)))
+
     def forces(self, out=None):
         if out is None:
             out = np.empty((self.N, 3))
@@ -330,8 +355,9 @@ class _Context:
         self._check(self.lib.rbl_set_phase_timing(self.h, int(bool(enable))))
 
     def phase_times(self, reset=False):
-        """(ms per phase [integrate, rebuild, force kernel, force reduction], timed steps)."""
-        ms = (ctypes.c_double * 4)()
+        """(ms per phase [integrate, cell sort, list build, force kernel, force reduction],
+        timed steps)."""
+        ms = (ctypes.c_double * 5)()
         n = ctypes.c_longlong()
         self._check(self.lib.rbl_phase_times(self.h, ms, ctypes.byref(n), int(bool(reset))))
         return list(ms), n.value

@@ -29,7 +29,8 @@ def _replicas():
     spec = [(500, 0.9, 1.0), (1000, 0.8, 1.5), (2113, 0.6, 2.0), (777, 0.75, 1.2), (3001, 0.85, 1.8)]
     out = []
     for r, (N, rho, T) in enumerate(spec):
-        x, L = inputs.fcc(N, rho, 0.2, seed=40 + r)
+        # jitter 0.05: larger jitter puts pairs near 0.5 sigma, where a dt = 0.005 step blows up
+        x, L = inputs.fcc(N, rho, 0.05, seed=40 + r)
         v = inputs.maxwell_boltzmann(N, T, seed=40 + r)
         out.append(inputs.Replica(N, rho, T, 40 + r, x, v, L))
     return out
@@ -139,7 +140,7 @@ def test_multi_chunk_replica_matches_single_context(precision):
     spec = [(900, 0.8, 1.2), (40000, 0.8, 1.5), (1500, 0.7, 1.0)]
     reps = []
     for r, (N, rho, T) in enumerate(spec):
-        x, L = inputs.fcc(N, rho, 0.2, seed=70 + r)
+        x, L = inputs.fcc(N, rho, 0.05, seed=70 + r)
         reps.append(rbl.Replica(x, inputs.maxwell_boltzmann(N, T, seed=70 + r), L, T, 70 + r))
     ens = rbl.Ensemble(reps, precision=precision, **SHARED)
     ens.step(12)

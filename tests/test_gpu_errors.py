@@ -7,6 +7,11 @@ status.
 - a core row longer than its capacity -> RBL_EOVERFLOW (rows truncated, counts kept);
 - a stencil population beyond the mask capacity -> RBL_EOVERFLOW;
 - non-finite input positions -> RBL_ENONFINITE at rbl_set_state;
+- finite input that turns bad during a step (two particles 0.05 sigma apart, or at
+  the same place): the binary32 force leaves the fixed-point range or is NaN (FP32
+  path), or the kicked particle jumps more than a box length (FP64 path) ->
+  RBL_ENONFINITE from rbl_step, with every kernel still inside its arrays (images are
+  32-bit integers whatever the positions, so cells and rows stay in range);
 - the capacities sized for the density pass (the same system with derived caps).
 """
 import numpy as np
@@ -61,4 +66,21 @@ def test_derived_capacities_pass(fluid):
     x, v, L = fluid
     s = rbl.System(x, v, L, **ARGS)
     s.step(5)
+    assert np.isfinite(s.forces()).all()
+
+
+@pytest.mark.parametrize("precision", [rbl.RBL_FP32, rbl.RBL_FP64])
+@pytest.mark.parametrize("gap", [0.05, 0.0])
+def test_overlap_mid_run(fluid, precision, gap):
+    """Finite positions are accepted; the first step reports the blow-up."""
+    x, v, L = fluid
+    y = x.copy()
+    y[1] = y[0] + np.array([gap, 0.0, 0.0])  # particle 1 moved next to (or onto) particle 0
+    s = rbl.System(y, v, L, precision=precision, **ARGS)
+    with pytest.raises(rbl.RblError) as e:
+        s.step(1)
+    assert e.value.status == 4, str(e.value)
+    # the context still answers: a new state loads and steps
+    s.set_state(x, v)
+    s.step(2)
     assert np.isfinite(s.forces()).all()

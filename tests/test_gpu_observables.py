@@ -53,7 +53,7 @@ def test_scalars_match_their_definitions():
 def test_async_equals_sync():
     reps = []
     for r, (N, rho, T) in enumerate([(700, 0.8, 1.2), (1500, 0.7, 1.8), (2049, 0.85, 1.0)]):
-        x, L = inputs.fcc(N, rho, 0.2, seed=90 + r)
+        x, L = inputs.fcc(N, rho, 0.05, seed=90 + r)
         reps.append(rbl.Replica(x, inputs.maxwell_boltzmann(N, T, seed=90 + r), L, T, 90 + r))
     ens = rbl.Ensemble(reps, r_c=RC, r_s=RS, skin=SKIN, p=P, dt=DT, gamma=1.0)
     buf = ens.obs_buffer()
