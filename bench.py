@@ -36,6 +36,16 @@ WORKLOAD = dict(name="lj_fluid_N1048576_rho0.8_T1.5_rc1.5_rs3.5_skin0.3_p10_nvt"
 FORCE_KERNEL = "k_force<0, true, false, 10, false>"  # RBL, FP32, no energy, p = 10, LJ
 FORCE_KERNEL_EWALD = "k_force<0, true, false, 10, true>"  # the same with the Ewald real-space term
 EWALD_ALPHA = 1.0  # the charged fluid's splitting parameter: erfc(alpha r_s) = 7e-7 at r_s = 3.5
+# Untimed steps between the start (FCC lattice) and every timed region, on top of
+# --warmup: the rebuild rate settles within ~100 steps (one rebuild every ~5 steps at
+# T* = 1.5), so the timed steps measure the steady state whatever --warmup is.
+EQUIL_STEPS = 200
+
+
+def phase_dict(pm, n):
+    """Per-step milliseconds of the five timed phases (rbl_phase_times)."""
+    names = ("integrate", "cell_sort", "list_build", "force_kernel", "force_reduce")
+    return {k: pm[q] / n for q, k in enumerate(names)}
 
 
 def parse():
@@ -173,16 +183,18 @@ def load_peaks():
 
 
 def load_traffic(N, name="force_kernel_traffic.json"):
-    """DRAM bytes per launch of the force kernel from the committed ncu summary, if it
-    was taken on the current force-kernel and list-build sources (else None).  The capture is of a smaller
-    system; traffic grows in proportion to N, so it is scaled per particle."""
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it was taken
+    on the current sources of that kernel (the record names the digest it depends on:
+    _build.force_digest by default, or _build.build_digest), else None.  The figure is
+    per particle: traffic grows in proportion to N."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             d = json.load(fh)
         from paper_2105_04884_gb300 import _build
 
-        if d.get("source_sha") != _build.force_digest():
+        digest = getattr(_build, d.get("digest", "force_digest"))
+        if d.get("source_sha") != digest():
             return None
         return float(d["dram_bytes_per_particle"]) * N
     except Exception:
@@ -308,7 +320,7 @@ def ensemble_bench(a, rank, world, timed):
                   cells_per_cutoff=e["K"], precision=rbl.RBL_FP32)
     ntot = sum(rp.N for rp in reps)
     ens = rbl.Ensemble(reps, **shared)
-    ens.step(a.warmup)
+    ens.step(a.warmup + EQUIL_STEPS)
     ens_cfg = ens.autotune(trials=3)
     K = a.ensemble_steps
     ms, _ = timed(ens, K, phases=False)
@@ -608,12 +620,12 @@ def ewald_bench(a, world, x, v, L, common, timed):
     out = {"workload": "charged LJ fluid: headline positions + neutral random +-1 charges", "alpha": EWALD_ALPHA}
     for name, kw in (("rbl", {}), ("full_list", {"full_list": True})):
         s = rbl.System(x, v, L, charges=q, **dict(ew, **kw))
-        s.step(a.warmup)
+        s.step(a.warmup + EQUIL_STEPS)
         s.autotune(trials=3)
         _, (pm, n) = timed(s, a.steps, phases=True)
         ms, _ = timed(s, a.steps, phases=False)
         out[name] = {"value": whole_job_rate(N, a.steps, world, ms), "ms_per_step": ms / a.steps,
-                     "force_kernel_ms": pm[2] / n, "rebuild_chain_ms": pm[1] / n}
+                     "force_kernel_ms": pm[3] / n, "rebuild_chain_ms": (pm[1] + pm[2]) / n}
         del s
         torch.cuda.empty_cache()
     out["speedup_vs_full_list"] = out["rbl"]["value"] / out["full_list"]["value"]
@@ -677,10 +689,11 @@ def run_ours(a, rank, world, local):
         wname = "charged_" + w["name"] + "_ewald_alpha%g" % EWALD_ALPHA
         kname, qself = FORCE_KERNEL_EWALD, 4
     s = rbl.System(x, v, L, **common)
-    s.step(a.warmup)
+    s.step(a.warmup + EQUIL_STEPS)
     tuned = s.autotune(trials=3)  # launch shapes only: no result depends on them
     # per-phase breakdown (direct launches bracketed by CUDA events) for the roofline,
     # then the headline: the same K steps as the library runs them, graph replays
+    obs0 = s.observables()
     ms_phase, (phase_ms, nsteps) = timed(s, a.steps, phases=True)
     obs1 = s.observables()
     clocks = Clocks(local)
@@ -690,20 +703,42 @@ def run_ours(a, rank, world, local):
     obs = s.observables()
     value = whole_job_rate(N, a.steps, world, ms)
     rebuilds = obs["n_rebuild"] - obs1["n_rebuild"]
-
-    # roofline of the force kernel: algorithmic bytes per particle of the data it must
-    # move -- own position 16, row counts and home cell 12, core row 4 n_c, the shell
-    # mask words of the home cell's stencil 4 ceil(M_c / 32), the home cell's segment
-    # table shared by the particles of the cell 16 S ncell / N, force out 24
-    nc, p = obs["Nc_mean"], w["p"]
-    import math as _m
-    S = 25 if w["K"] == 2 else (2 * w["K"] + 1) ** 2
-    ncell = int(_m.floor(L[0] * w["K"] / (w["rs"] + w["skin"]))) ** 3
-    alg_bytes_pp = 16 + 12 + 4 * nc + 4 * _m.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24 + qself
-    t_force = phase_ms[2] / nsteps * 1e-3
-    achieved = alg_bytes_pp * N / t_force / 1e9
+    rebuilds_phase = obs1["n_rebuild"] - obs0["n_rebuild"]
+    ph = phase_dict(phase_ms, nsteps)
     peak, peak_kind = load_peaks()
-    traffic = load_traffic(N, "force_kernel_traffic_ewald.json" if ewald else "force_kernel_traffic.json")
+    nc, ns, p = obs["Nc_mean"], obs["Ns_mean"], w["p"]
+    # Roofline of the RBL force kernel (K4).  Algorithmic bytes per particle, the data
+    # the method must move: own position 16, core row 4 n_c, N_s 4, the p sampled shell
+    # entries 4 p, force out 24.  The bytes of this build's layout (row counts and home
+    # cell 12, core row, every shell mask word of the home cell's stencil 4 ceil(M_c/32),
+    # the cell's share of the segment table 16 S ncell / N, force 24) and the DRAM
+    # traffic ncu measured are reported beside it.
+    S = 25 if w["K"] == 2 else (2 * w["K"] + 1) ** 2
+    ncell = int(math.floor(L[0] * w["K"] / (w["rs"] + w["skin"]))) ** 3
+    alg_force = 16 + 4 * nc + 4 + 4 * p + 24 + qself
+    layout_force = 16 + 12 + 4 * nc + 4 * math.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24 + qself
+    t_force = ph["force_kernel"] * 1e-3
+    traffic_f = load_traffic(N, "force_kernel_traffic_ewald.json" if ewald else "force_kernel_traffic.json")
+    roof_force = {"kernel": kname, "bound": "hbm", "achieved": alg_force * N / t_force / 1e9, "peak": peak,
+                  "unit": "GB/s", "frac": alg_force * N / t_force / 1e9 / peak, "peak_source": peak_kind,
+                  "algorithmic_bytes_per_particle": alg_force, "layout_bytes_per_particle": layout_force,
+                  "layout_frac": layout_force * N / t_force / 1e9 / peak,
+                  "traffic": traffic_f, "traffic_per": "launch", "ms_per_launch": ph["force_kernel"]}
+    # Roofline of the list build (K3), per rebuild: own position 16 and the rows, core
+    # and shell, as 4-byte entries 4 (n_c + N_s) (the same bytes as the survey's
+    # estimate of ~800 B per particle per rebuild).  Its launches inside the phase-timed
+    # steps that did not rebuild return at once; the phase total is divided by the
+    # rebuilds (a slight overestimate of the per-rebuild time).
+    alg_build = 16 + 4 * (nc + ns)
+    t_build = ph["list_build"] * nsteps / max(rebuilds_phase, 1) * 1e-3
+    traffic_b = load_traffic(N, "list_build_traffic.json")
+    roof_build = {"kernel": "k_build_lists<0> (core row + shell mask, one warp per home cell)", "bound": "hbm",
+                  "achieved": alg_build * N / t_build / 1e9, "peak": peak, "unit": "GB/s",
+                  "frac": alg_build * N / t_build / 1e9 / peak, "peak_source": peak_kind,
+                  "algorithmic_bytes_per_particle": alg_build, "traffic": traffic_b, "traffic_per": "launch",
+                  "ms_per_launch": t_build * 1e3, "launches_timed": rebuilds_phase,
+                  "share_of_step": ph["list_build"] / sum(ph.values())}
+    dominant = roof_build if ph["list_build"] >= ph["force_kernel"] else roof_force
     result = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -712,22 +747,21 @@ def run_ours(a, rank, world, local):
                    "skin": w["skin"], "p": p, "dt": w["dt"], "gamma": w["gamma"], "cells_per_cutoff": w["K"],
                    "pair_math": "fp32 + int64 fixed-point sums", "integration": "fp64 BAOAB",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set > L2 (lists %.0f MB)" % (4 * N * (nc + obs["Ns_mean"]) / 1e6),
+                   "equilibration_steps": a.warmup + EQUIL_STEPS,
+                   "l2": "working set > L2 (lists %.0f MB)" % (4 * N * (nc + ns) / 1e6),
                    "timed_path": "rbl_step(K): CUDA graph replays, one per step (the rebuild chain behind a "
                                  "device-side IF node)"},
         # per step: integrate, the rebuild condition, force kernel and its reduction;
         # the 12 rebuild-chain kernels on the steps that rebuild; on the last step the
         # energy sums' chunk reduction and the closing half-kick
         "gpu_launches": 4 * a.steps + 12 * rebuilds + 2,
-        "phases_ms_per_step": {"integrate": phase_ms[0] / nsteps, "rebuild_chain": phase_ms[1] / nsteps,
-                               "force_kernel": phase_ms[2] / nsteps, "force_reduce": phase_ms[3] / nsteps},
+        "phases_ms_per_step": ph,
         "phase_timed_ms_per_step": ms_phase / a.steps,
         "rebuilds_in_timed_region": rebuilds,
-        "rows": {"core_mean": nc, "shell_mean": obs["Ns_mean"], "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"]},
-        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_particle": alg_bytes_pp,
-                     "traffic": traffic, "traffic_per": "launch"},
+        "rows": {"core_mean": nc, "shell_mean": ns, "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"],
+                 "stencil_mean": obs["Mc_mean"]},
+        "roofline": dominant,
+        "rooflines": {"k_build_lists": roof_build, "k_force": roof_force},
         "clocks": clk,
         "launch_config": tuned,
     }
@@ -736,41 +770,45 @@ def run_ours(a, rank, world, local):
         del s
         torch.cuda.empty_cache()
         sf = rbl.System(x, v, L, full_list=True, **common)
-        sf.step(a.warmup)
+        sf.step(a.warmup + EQUIL_STEPS)
         sf.autotune(trials=3)
         _, (pmf, nf) = timed(sf, a.steps, phases=True)
         msf, _ = timed(sf, a.steps, phases=False)
         vf = whole_job_rate(N, a.steps, world, msf)
         of = sf.observables()
-        result["full_list"] = {"value": vf, "ms_per_step": msf / a.steps,
-                               "force_kernel_ms": pmf[2] / nf, "full_mean": of["Ns_mean"]}
+        result["full_list"] = {"value": vf, "ms_per_step": msf / a.steps, "phases_ms_per_step": phase_dict(pmf, nf),
+                               "force_kernel_ms": pmf[3] / nf, "full_mean": of["Ns_mean"],
+                               "pairs_per_s": N * of["Ns_mean"] / (pmf[3] / nf * 1e-3)}
         result["speedup_vs_full_list"] = value / vf
         del sf
         torch.cuda.empty_cache()
-        # the same workload at r_c = 2.0 (where the block-averaged P, U and g(r) of the
-        # RBL trajectory match the full list's; see "matched_physics")
+        # the same workload at r_c = 2.0, where the block-averaged P, U and g(r) of the
+        # RBL trajectory match the full list's (the metric's "matched pressure/g(r)")
         s2 = rbl.System(x, v, L, **dict(common, r_c=2.0))
-        s2.step(a.warmup)
+        s2.step(a.warmup + EQUIL_STEPS)
         s2.autotune(trials=3)
         _, (pm2, n2) = timed(s2, a.steps, phases=True)
         ms2, _ = timed(s2, a.steps, phases=False)
         v2 = whole_job_rate(N, a.steps, world, ms2)
-        result["rbl_rc2.0"] = {"value": v2, "ms_per_step": ms2 / a.steps, "force_kernel_ms": pm2[2] / n2,
-                               "speedup_vs_full_list": v2 / vf}
+        result["rbl_rc2.0"] = {"value": v2, "ms_per_step": ms2 / a.steps, "force_kernel_ms": pm2[3] / n2,
+                               "phases_ms_per_step": phase_dict(pm2, n2), "speedup_vs_full_list": v2 / vf}
+        result["value_matched_physics"] = v2
+        result["speedup_matched_physics"] = v2 / vf
+        result["matched_physics_setting"] = ("r_c = 2.0, p = 10 (block-averaged P, U and g(r) within error bars of "
+                                             "the full list; r_c = 1.5 heats the system)")
         del s2
         torch.cuda.empty_cache()
         # the paper's own sampling pool on the same workload: no shell list (the list
         # build tests only the 27 nearest cells), batch from the whole cell stencil
         s3 = rbl.System(x, v, L, **dict(common, sampling=rbl.RBL_SAMPLE_STENCIL))
-        s3.step(a.warmup)
+        s3.step(a.warmup + EQUIL_STEPS)
         s3.autotune(trials=3)
         _, (pm3, n3) = timed(s3, a.steps, phases=True)
         ms3, _ = timed(s3, a.steps, phases=False)
         o3 = s3.observables()
         v3 = whole_job_rate(N, a.steps, world, ms3)
         result["rbl_stencil_pool"] = {"value": v3, "ms_per_step": ms3 / a.steps,
-                                      "phases_ms_per_step": {"integrate": pm3[0] / n3, "rebuild_chain": pm3[1] / n3,
-                                                             "force_kernel": pm3[2] / n3, "force_reduce": pm3[3] / n3},
+                                      "phases_ms_per_step": phase_dict(pm3, n3),
                                       "pool_mean": o3["Ns_mean"], "speedup_vs_full_list": v3 / vf,
                                       "speedup_vs_shell_list": v3 / value}
         del s3
@@ -784,10 +822,11 @@ def run_ours(a, rank, world, local):
 
         se = rbl.System(x, v, L, **common)
         se.set_phase_timing(False)
-        se.step(a.warmup)
+        se.step(a.warmup + EQUIL_STEPS)
         se.autotune(trials=3)
-        xh = torch.from_numpy(x).pin_memory()
-        vh = torch.from_numpy(v).pin_memory()
+        xe, ve, step_e = se.get_state()  # the equilibrated state is what a user's loop uploads
+        xh = torch.from_numpy(xe).pin_memory()
+        vh = torch.from_numpy(ve).pin_memory()
         xo = torch.empty_like(xh).pin_memory()
         vo = torch.empty_like(vh).pin_memory()
         osz = ctypes.sizeof(rbl.rbl_obs)
@@ -798,8 +837,8 @@ def run_ours(a, rank, world, local):
             sync_all()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()), 0,
-                                           0))
+            se._check(se.lib.rbl_set_state(se.h, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(vh.data_ptr()),
+                                           step_e, 0))
             for k in range(a.steps):
                 if mode == "async":
                     se._check(se.lib.rbl_step_async(se.h, 1))

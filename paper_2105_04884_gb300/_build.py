@@ -58,6 +58,16 @@ def force_digest() -> str:
     return _digest([os.path.join(CSRC, f) for f in FORCE_SOURCES])
 
 
+# The sources that fix the list build's code (its traffic figure stays valid while
+# these are unchanged).
+BUILD_SOURCES = ("rbl_build.cu", "rbl_internal.cuh")
+
+
+def build_digest() -> str:
+    """sha256 of the list build's sources (see BUILD_SOURCES)."""
+    return _digest([os.path.join(CSRC, f) for f in BUILD_SOURCES])
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB):
