@@ -273,7 +273,7 @@ __global__ void k_copy_back(View v, int conditional)
 // once) and tests each against every particle of the cell:
 //   core : r2 <  (r_c + skin)^2                         -> explicit list (ballot rank)
 //   shell: max(r_c - skin, 0)^2 <= r2 < (r_s + skin)^2  -> mask word (ballot)
-//   full : r2 <  (r_s + skin)^2   (full_list mode, in the mask)
+//   full : r2 <  (r_s + skin)^2   (full_list mode: explicit row-major rows, no mask)
 // Candidates are visited in canonical order, so list order and bit order are the
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
 // k.  Row lengths are counted past the core capacity.  With stencil-pool sampling
@@ -282,7 +282,7 @@ __global__ void k_copy_back(View v, int conditional)
 // itself; the segment table still spans the whole stencil, for the batch.
 constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
-// LIST: kListShell (core row + shell mask), kListFull (full-list mask), kListPool
+// LIST: kListShell (core row + shell mask), kListFull (full-list rows), kListPool
 // (core row only; stencil-pool sampling), fixed at compile time so that the pair-test
 // loop carries no mode branches.
 enum { kListShell = 0, kListFull = 1, kListPool = 2 };
@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
     RepScalars &rsc = v.rs[r];
     constexpr bool pool = LIST == kListPool; // no masks: the stencil population is not bounded by them
-    if (!pool && M > v.Mcap) {
+    constexpr bool full = LIST == kListFull; // no masks either: explicit rows
+    if (!pool && !full && M > v.Mcap) {
         // too many candidates for the masks: flag it and leave these particles with
         // empty rows so that no kernel decodes a mask that was not written
         for (int i = s0 + lane; i < s1; i += 32) {
@@ -401,8 +402,8 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
         Mloop = pre[nseg];
     }
     const int nchunk = (Mloop + 31) >> 5;
-    constexpr bool full = LIST == kListFull;
     const size_t N = (size_t)v.N;
+    const unsigned lt_mask = (1u << lane) - 1u;
     int wmc = 0, wms = 0;
     unsigned long long wsc = 0ull, wss = 0ull;
     for (int base = s0; base < s1; base += 32) {
@@ -428,9 +429,21 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             for (int q = 0; q < mm; ++q) {
                 PairGeom g = pair_geom(s_pos[warp][q], pj, h);
                 const bool other = valid && j != base + q;
-                if constexpr (!pool) {
-                    const bool in_shell = full ? other && g.r2 < v.t_cut_list
-                                               : other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
+                if constexpr (full) {
+                    // the full row of particle base + q, in candidate order: each member
+                    // lane writes its entry at the particle's count plus its rank in the
+                    // ballot (consecutive addresses of the row)
+                    const bool in = other && g.r2 < v.t_cut_list;
+                    const unsigned bf = __ballot_sync(0xffffffffu, in);
+                    const int n0q = __shfl_sync(0xffffffffu, my_nc, q);
+                    if (in) {
+                        const int rk = n0q + __popc(bf & lt_mask);
+                        if (rk < v.cap_c) v.core[(size_t)(base + q) * (size_t)v.cap_c + rk] = j;
+                    }
+                    if (lane == q) my_nc += __popc(bf);
+                }
+                if constexpr (!pool && !full) {
+                    const bool in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
                     const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
                     my_shell = lane == q ? bs : my_shell;
                 }
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
                 }
             }
             __syncwarp();
-            if (lane < mm) {
+            if (lane < mm && !full) {
                 if (!pool) v.mask[(size_t)k * N + i_me] = my_shell; // coalesced across lanes
                 my_ns += __popc(my_shell);
                 while (my_core) { // core row in candidate order
@@ -455,6 +468,11 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
         }
         if (lane < mm) {
             if (pool) my_ns = M - 1; // the pool: every other particle of the stencil
+            if (full) { // the full row's length, counted as the shell's
+                my_ns = my_nc;
+                my_nc = 0;
+                if (my_ns > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
+            }
             v.n_core[i_me] = my_nc;
             v.n_shell[i_me] = my_ns;
             if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);

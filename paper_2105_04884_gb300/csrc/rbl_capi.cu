@@ -42,7 +42,8 @@ struct Plan {
 // Cell grid and candidate statistics of one replica.
 struct Geo {
     int n3[3], nofs3[3], S, ncell, mcap;
-    double core_mean;
+    double core_mean;  // mean core row (r < r_c + skin)
+    double full_mean;  // mean full row (r < r_s + skin)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -147,6 +148,7 @@ Geo replica_geo(const rbl_params *p, int N)
     int mcap = p->cap_stencil > 0 ? p->cap_stencil : (int)std::ceil(1.3 * rho * span + 96.0);
     g.mcap = mcap > N ? N : mcap;
     g.core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
+    g.full_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_s + p->skin, 3);
     return g;
 }
 
@@ -156,7 +158,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.R = R;
     long long slots = 0, cells = 0, n_real = 0, max_slots = 0;
     int S = 1, mcap = 32;
-    double core_mean = 0.0;
+    double core_mean = 0.0, full_mean = 0.0;
     for (int r = 0; r < R; ++r) {
         Geo g = replica_geo(&prm[r], Ns[r]);
         slots += round_up_ll(Ns[r], kTile);
@@ -166,6 +168,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
         S = g.S > S ? g.S : S;
         mcap = g.mcap > mcap ? g.mcap : mcap;
         core_mean = g.core_mean > core_mean ? g.core_mean : core_mean;
+        full_mean = g.full_mean > full_mean ? g.full_mean : full_mean;
     }
     const rbl_params *p = &prm[0];
     P.N = (int)slots;
@@ -174,8 +177,12 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     P.n_real = n_real;
     P.S = S;
     P.Mcap = round_up(mcap, 32);
-    P.W = prm[0].sampling == RBL_SAMPLE_STENCIL ? 0 : P.Mcap / 32; // the stencil pool needs no masks
-    P.cap_c = p->full_list ? 1 : (p->cap_core > 0 ? p->cap_core : round_up((int)std::ceil(1.6 * core_mean + 24.0), 8));
+    // the stencil pool and the full list need no masks; the full list's rows are
+    // explicit (row-major) in the core array, cap_c entries each
+    P.W = (prm[0].sampling == RBL_SAMPLE_STENCIL || p->full_list) ? 0 : P.Mcap / 32;
+    const double row_mean = p->full_list ? full_mean : core_mean;
+    P.cap_c = p->cap_core > 0 ? round_up(p->cap_core, p->full_list ? 4 : 1)
+                              : round_up((int)std::ceil(1.6 * row_mean + 24.0), 8);
     P.n_scan_blocks = (P.ncell + 2047) / 2048;
     P.pchunks = (int)((max_slots / kMinBlock + kChunkGroups - 1) / kChunkGroups);
     const size_t Nz = (size_t)P.N;
@@ -981,14 +988,17 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
             return RBL_EOVERFLOW;
         }
     }
-    if (kind == 0) {
+    if (kind == 0 || v.full_list) {
+        // explicit rows: core[k][N] (column-major), or the full list's rows core[N][cap_c]
         std::vector<int> core(N * (size_t)v.cap_c);
         CK(cudaMemcpy(core.data(), v.core, core.size() * 4, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < N; ++i) {
             if (row_of[i] < 0) continue;
             const size_t t = (size_t)row_of[i];
             counts[t] = cnt[i];
-            for (int k = 0; k < cnt[i]; ++k) rows[t * cap + k] = tag[core[(size_t)k * N + i]];
+            const int n = cnt[i] < v.cap_c ? cnt[i] : v.cap_c;
+            for (int k = 0; k < n; ++k)
+                rows[t * cap + k] = tag[v.full_list ? core[i * (size_t)v.cap_c + k] : core[(size_t)k * N + i]];
         }
         return RBL_OK;
     }
@@ -1058,6 +1068,12 @@ rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, i
         }
         counts[k] = cnt;
         int *out = rows + (size_t)k * cap;
+        if (kind == 1 && v.full_list) { // row i of core[N][cap_c]
+            const int n = cnt < v.cap_c ? cnt : v.cap_c;
+            if (n > 0) CK(cudaMemcpy(entries.data(), v.core + i * (size_t)v.cap_c, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < n; ++q) out[q] = tag[entries[q]];
+            continue;
+        }
         if (kind == 0) {
             // column i of core[cap_c][N]
             const int nc = cnt < v.cap_c ? cnt : v.cap_c;
@@ -1088,6 +1104,10 @@ rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, i
 rbl_status rbl_get_batch(rbl_ctx *ctx, long long step, int *batch, int *counts)
 {
     if (!ctx || !batch || !counts || step < 0) return RBL_EINVAL;
+    if (ctx->view.full_list) {
+        set_err(ctx, "the full list draws no batches");
+        return RBL_EINVAL;
+    }
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
     const View &v = ctx->view;

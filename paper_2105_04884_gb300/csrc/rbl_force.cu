@@ -186,7 +186,12 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
         float qf = __fdiv_rn(__fsqrt_rn(g.r2), dr);
         if (qf < (float)nbins) atomicAdd(&hr[(int)qf], 1ull);
     };
-    if (!v.full_list) {
+    if (v.full_list) { // explicit row-major rows
+        const int n = min(v.n_shell[i], v.cap_c);
+        for (int k = 0; k < n; ++k) count(v.core[(size_t)i * (size_t)v.cap_c + k], false);
+        return;
+    }
+    {
         int nc = min(v.n_core[i], v.cap_c);
         for (int k = 0; k < nc; ++k) count(v.core[(size_t)k * N + i], true);
     }

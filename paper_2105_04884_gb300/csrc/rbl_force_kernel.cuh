@@ -192,7 +192,7 @@ __device__ __forceinline__ void sort_small(int *S, int n)
 }
 
 // EWALD: the pair is LJ plus the Ewald real-space term q_i q_j erfc(alpha r) / r.
-// MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (mask);
+// MODE 0: RBL (core list + sampled shell mask); MODE 1: full list (explicit rows);
 // MODE 2: exact observables -- the core list and every shell (or full) mask entry,
 // or every pool member, unsampled, energy and virial only (no force written, no
 // total force); MODE 3: RBL with the batch drawn from the stencil pool.
@@ -458,8 +458,30 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                 }
                 acc.template pairs<kGather>(v, pi, i, jj, min(kGather, M - c0), 1);
             }
-        } else if (MODE == 1 || MODE == 2) {
-            // every mask entry, kGather members at a time
+        } else if ((MODE == 1 || MODE == 2) && v.full_list) {
+            // the full list's explicit row (row-major, cap_c entries of which the first
+            // n are set), kGather members at a time; four indices per 16-byte load
+            const int *row = v.core + (size_t)i * (size_t)v.cap_c;
+            const int n = min(ns, v.cap_c);
+            for (int k0 = 0; k0 < n; k0 += kGather) {
+                int jj[kGather];
+                if constexpr (kGather % 4 == 0) {
+#pragma unroll
+                    for (int u = 0; u < kGather; u += 4) {
+                        const int4 e = __ldg((const int4 *)(row + k0 + u));
+                        jj[u] = k0 + u < n ? e.x : i;
+                        jj[u + 1] = k0 + u + 1 < n ? e.y : i;
+                        jj[u + 2] = k0 + u + 2 < n ? e.z : i;
+                        jj[u + 3] = k0 + u + 3 < n ? e.w : i;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kGather; ++u) jj[u] = k0 + u < n ? row[k0 + u] : i;
+                }
+                acc.template pairs<kGather>(v, pi, i, jj, n - k0, 1);
+            }
+        } else if (MODE == 2) {
+            // every shell mask entry, kGather members at a time
             int w = 0;
             unsigned word = ns > 0 ? mask_word(0) : 0u;
             for (int k0 = 0; k0 < ns; k0 += kGather) {
