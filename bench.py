@@ -776,9 +776,18 @@ def run_ours(a, rank, world, local):
         msf, _ = timed(sf, a.steps, phases=False)
         vf = whole_job_rate(N, a.steps, world, msf)
         of = sf.observables()
+        # the full-list force kernel's roofline: own position 16, the row 4 N_full, force 24
+        alg_full = 16 + 4 * of["Ns_mean"] + 24
+        t_full = pmf[3] / nf * 1e-3
         result["full_list"] = {"value": vf, "ms_per_step": msf / a.steps, "phases_ms_per_step": phase_dict(pmf, nf),
                                "force_kernel_ms": pmf[3] / nf, "full_mean": of["Ns_mean"],
-                               "pairs_per_s": N * of["Ns_mean"] / (pmf[3] / nf * 1e-3)}
+                               "pairs_per_s": N * of["Ns_mean"] / t_full,
+                               "roofline": {"kernel": "k_force<1, true, false, 0, false> (explicit full rows)",
+                                            "bound": "hbm", "achieved": alg_full * N / t_full / 1e9, "peak": peak,
+                                            "unit": "GB/s", "frac": alg_full * N / t_full / 1e9 / peak,
+                                            "algorithmic_bytes_per_particle": alg_full,
+                                            "traffic": load_traffic(N, "full_list_force_traffic.json"),
+                                            "traffic_per": "launch"}}
         result["speedup_vs_full_list"] = value / vf
         del sf
         torch.cuda.empty_cache()
