@@ -181,7 +181,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     // explicit (row-major) in the core array, cap_c entries each
     P.W = (prm[0].sampling == RBL_SAMPLE_STENCIL || p->full_list) ? 0 : P.Mcap / 32;
     const double row_mean = p->full_list ? full_mean : core_mean;
-    P.cap_c = p->cap_core > 0 ? round_up(p->cap_core, p->full_list ? 4 : 1)
+    P.cap_c = p->cap_core > 0 ? round_up(p->cap_core, p->full_list ? 8 : 1)
                               : round_up((int)std::ceil(1.6 * row_mean + 24.0), 8);
     P.n_scan_blocks = (P.ncell + 2047) / 2048;
     P.pchunks = (int)((max_slots / kMinBlock + kChunkGroups - 1) / kChunkGroups);

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kBlock) k_force_finish(View v, int fp32, int e
     const int r = blockIdx.x;
     const Box &b = v.box[r];
     const int ng = b.slots / kMinBlock;
-    const int nb = (fp32 && !energy) ? 0 : (ng + kChunkGroups - 1) / kChunkGroups;
+    // the FP32 path's sums are exact integers in rs (forces, energies): no partials
+    const int nb = (fp32 && !exact) ? 0 : (ng + kChunkGroups - 1) / kChunkGroups;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
 #pragma unroll
@@ -94,8 +95,15 @@ __global__ void __launch_bounds__(kBlock) k_force_finish(View v, int fp32, int e
             rsc.fcor[a] = m;
         }
         if (energy) {
-            rsc.energy = tot[3];
-            rsc.virial = tot[4];
+            if (fp32) {
+                const double sc = 1.0 / 16777216.0;
+                rsc.energy = (double)(long long)rsc.ew_q[0] * sc;
+                rsc.virial = (double)(long long)rsc.ew_q[1] * sc;
+                rsc.ew_q[0] = rsc.ew_q[1] = 0ull;
+            } else {
+                rsc.energy = tot[3];
+                rsc.virial = tot[4];
+            }
         }
         if (r == 0) v.sc->step += (unsigned long long)advance;
     }
@@ -230,9 +238,11 @@ cudaError_t launch_force_kernel(const View &v, int step_offset, bool energy, cud
 cudaError_t launch_force_finish(const View &v, int advance, bool energy, cudaStream_t s)
 {
     bool fp32 = v.precision == RBL_FP32;
-    const bool sums = energy || !fp32; // FP64 force sums or energies to reduce
-    if (sums) k_force_chunks<<<dim3(v.pchunks, v.R), kChunkGroups, 0, s>>>(v);
-    k_force_finish<<<v.R, sums ? kBlock : 32, 0, s>>>(v, fp32 ? 1 : 0, sums ? 1 : 0, v.subtract, advance, 0);
+    // FP64 force and energy sums are reduced from per-group partials; the FP32 path's
+    // are exact integers already
+    if (!fp32) k_force_chunks<<<dim3(v.pchunks, v.R), kChunkGroups, 0, s>>>(v);
+    k_force_finish<<<v.R, fp32 ? 32 : kBlock, 0, s>>>(v, fp32 ? 1 : 0, (energy || !fp32) ? 1 : 0, v.subtract, advance,
+                                                      0);
     return cudaGetLastError();
 }
 

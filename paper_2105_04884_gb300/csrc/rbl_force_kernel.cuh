@@ -214,16 +214,18 @@ static_assert(kMaskStage > 0 && (kMaskStage & (kMaskStage - 1)) == 0 && kMaskSta
               "kMaskStage must be a power of two no larger than 32");
 
 // Gather width and FP32 register cap per mode, measured on GB300 (the LJ fluid and
-// the charged fluid at N = 2^20, best block shape of each): shell sampling and the
-// full list, with or without the Ewald term, run fastest with 4 gathers in flight and
-// 64 registers (4 blocks of 256 threads per SM), the stencil pool with 12 and 80 (8
-// and 80 with the Ewald term); the energy variants (last step of a call, one-step
-// calls) keep their energy and virial sums in 72.  The FP64 path needs up to 128
-// registers and runs at the FP64 rate anyway.
+// the charged fluid at N = 2^20, best block shape of each): shell sampling runs
+// fastest with 4 gathers in flight and 64 registers (4 blocks of 256 threads per SM),
+// the stencil pool with 12 and 80 (8 and 80 with the Ewald term), the full list's
+// explicit rows with 8 and 80 (0.61 -> 0.53 ms; 16 and 128: 0.52 ms); the energy
+// variants (last step of a call, one-step calls) keep their energy and virial sums in
+// 72.  The FP64 path needs up to 128 registers and runs at the FP64 rate anyway.
+// The full list's rows hold a multiple of 8 entries, so its 16-byte index loads stay
+// inside a row.
 template <int MODE, bool ENERGY, bool EWALD>
 struct ForceTuning {
-    static constexpr int gather = MODE == 3 ? (EWALD ? 8 : 12) : 4;
-    static constexpr int regs = MODE == 3 ? 80 : (ENERGY ? 72 : 64);
+    static constexpr int gather = MODE == 1 ? 8 : (MODE == 3 ? (EWALD ? 8 : 12) : 4);
+    static constexpr int regs = (MODE == 1 || MODE == 3) ? 80 : (ENERGY ? 72 : 64);
 };
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>
@@ -240,6 +242,7 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
     const int i = blockIdx.x * bd + t;
     const size_t N = (size_t)v.N;
     long long qv[3] = {0, 0, 0};
+    long long eq = 0, wq = 0;       // FP32 path, ENERGY: fixed-point energy and virial
     double f64[3] = {0.0, 0.0, 0.0};
     double e_i = 0.0, w_i = 0.0;
     bool live = false;
@@ -525,8 +528,14 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                 F[a * N + i] = qv[a];
             }
             if (ENERGY) {
-                e_i = 0.5 * ((double)acc.e32[0] + (double)s32 * (double)acc.e32[1]);
-                w_i = 0.5 * ((double)acc.w32[0] + (double)s32 * (double)acc.w32[1]);
+                // the particle's energy and virial estimates in binary32, halved
+                // exactly, then exactly in fixed point (scale 2^24): integer sums
+                // over particles are exact and order-free, and need no FP64 pipe
+                const float e = __fmul_rn(0.5f, __fmaf_rn(s32, acc.e32[1], acc.e32[0]));
+                const float w = __fmul_rn(0.5f, __fmaf_rn(s32, acc.w32[1], acc.w32[0]));
+                if (!(fabsf(e) < kEnergyRange) || !(fabsf(w) < kEnergyRange)) atomicOr(&v.sc->flags, kFlagNonFinite);
+                eq = __float2ll_rn(__fmul_rn(e, 16777216.0f));
+                wq = __float2ll_rn(__fmul_rn(w, 16777216.0f));
             }
         } else {
             double *F = (double *)v.F;
@@ -550,9 +559,12 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
             long long s = warp_sum(qv[a]);
             if (lane == 0 && s != 0) atomicAdd(&v.rs[r].fsum_q[a], (unsigned long long)s);
         }
-        if (ENERGY) {
-            double x[2] = {e_i, w_i};
-            group_sums<2>(x, v.partials, 3);
+        if (ENERGY) { // a warp's slots belong to one replica (replicas start on whole tiles)
+            const long long se = warp_sum(eq), sw = warp_sum(wq);
+            if (lane == 0) {
+                if (se != 0) atomicAdd(&v.rs[r].ew_q[0], (unsigned long long)se);
+                if (sw != 0) atomicAdd(&v.rs[r].ew_q[1], (unsigned long long)sw);
+            }
         }
     } else {
         double x[5] = {f64[0], f64[1], f64[2], e_i, w_i};

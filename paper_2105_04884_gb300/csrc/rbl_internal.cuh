@@ -33,6 +33,7 @@ constexpr int kMaxSeg = kMaxStencil * kMaxStencil;
 // the box in one step (moved more than a box length).
 enum : unsigned { kFlagOverflow = 1u, kFlagNonFinite = 2u, kFlagCellOverflow = 4u, kFlagRngLimit = 8u };
 constexpr float kFixedRange = 536870880.0f; // below 2^29: |4 F| stays inside the int32 split of FixedAcc
+constexpr float kEnergyRange = 274877906944.0f; // 2^38: |e 2^24| stays inside int64 with room for a sum
 
 // Context-wide scalars living in device memory (one instance in the workspace).
 struct DevScalars {
@@ -44,6 +45,8 @@ struct DevScalars {
 // Per-replica scalars living in device memory ([R] in the workspace).
 struct RepScalars {
     unsigned long long fsum_q[3];   // FP32 path: sum of fixed-point forces (mod 2^64)
+    unsigned long long ew_q[2];     // FP32 path: sums of the per-particle energy and virial
+                                    // estimates in fixed point (scale 2^24, mod 2^64)
     double fcor[3];                 // mean force subtracted from every particle
     long long fcor_q[3];            // FP32 path: the net force Q (fixed point) as Q = N fcor_q + fcor_r,
     long long fcor_r[3];            // 0 <= fcor_r < N; tags < fcor_r subtract fcor_q + 1, the rest fcor_q

@@ -55,6 +55,43 @@ def _relnorm(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _pair_uw(x, L, q, alpha, I, J):
+    """Pair energy LJ + q_i q_j erfc(alpha r)/r and virial r . f of pairs (I, J), and r^2."""
+    from scipy.special import erfc
+
+    d = x[J] - x[I]
+    d -= L * np.round(d / L)
+    r2 = (d * d).sum(1)
+    r = np.sqrt(r2)
+    ir6 = r2**-3
+    qq = q[I] * q[J]
+    ec = erfc(alpha * r) / r
+    u = 4 * (ir6 * ir6 - ir6) + qq * ec
+    w = 24 * (2 * ir6 * ir6 - ir6) + qq * (ec + 2 * alpha / np.sqrt(np.pi) * np.exp(-alpha * alpha * r2))
+    return u, w, r2
+
+
+def _scale_estimate(c, x, L, q, lists, batch, nb):
+    """1/2 the magnitude of the summed terms of the RBL energy and virial estimates:
+    core pairs r < r_c, batch pairs r_c <= r < r_s times s_i = N_s / p (the scale of a
+    rounded sum's error; the virial nearly cancels)."""
+    N, rc, rs, p = len(x), c["rc"], c["rs"], c["p"]
+    I = np.concatenate([np.full(len(lists.row("core", i)), i) for i in range(N)]).astype(np.int64)
+    J = np.concatenate([lists.row("core", i) for i in range(N)]).astype(np.int64)
+    u, w, r2 = _pair_uw(x, L, q, c["alpha"], I, J)
+    m = r2 < rc * rc
+    su, sw = np.abs(u[m]).sum(), np.abs(w[m]).sum()
+    ns = lists.n_shell
+    scale = np.where(ns > p, ns / p, 1.0)
+    Ib = np.concatenate([np.full(nb[i], i) for i in range(N)]).astype(np.int64)
+    Jb = np.concatenate([batch[i, : nb[i]] for i in range(N)]).astype(np.int64)
+    u, w, r2 = _pair_uw(x, L, q, c["alpha"], Ib, Jb)
+    m = (r2 >= rc * rc) & (r2 < rs * rs)
+    su += (scale[Ib[m]] * np.abs(u[m])).sum()
+    sw += (scale[Ib[m]] * np.abs(w[m])).sum()
+    return 0.5 * su, 0.5 * sw
+
+
 @pytest.fixture(scope="module", params=sorted(CASES))
 def case(request):
     c = CASES[request.param]
@@ -68,14 +105,15 @@ def test_rbl_forces_and_estimates(case, precision, tol):
     c, x, v, L, q, lists = case
     s = _system(c, x, v, L, q, precision=precision)
     F = s.forces()
-    Fo, ev, _, _ = oracle.rbl_forces(x, L, c["rc"], c["rs"], c["skin"], c["p"], c["seed"], 0, lists, q=q,
-                                     alpha=c["alpha"])
+    Fo, ev, ob, obn = oracle.rbl_forces(x, L, c["rc"], c["rs"], c["skin"], c["p"], c["seed"], 0, lists, q=q,
+                                        alpha=c["alpha"], want_batch=True)
     Fo = oracle.subtract_mean(Fo)
     assert _relnorm(F, Fo) <= tol
     obs = s.observables()
-    assert abs(obs["U_est"] - ev[0]) <= 10 * tol * abs(ev[0])
-    if precision == rbl.RBL_FP64:  # the virial sum cancels too much for a relative FP32 bar
-        assert abs(obs["W_est"] - ev[1]) <= 10 * tol * abs(ev[1])
+    # the estimates' bar: tol times the magnitude of the summed pair terms
+    su, sw = _scale_estimate(c, x, L, q, lists, ob, obn)
+    assert abs(obs["U_est"] - ev[0]) <= tol * su
+    assert abs(obs["W_est"] - ev[1]) <= tol * sw
 
 
 @pytest.mark.parametrize("full_list", [False, True])
