@@ -217,7 +217,15 @@ rbl_status rbl_forces(rbl_ctx *ctx, double *F_out, int ptr_is_device);
 /* Advances n >= 0 steps of Algorithm 1: velocity-Verlet kick/drift with the Langevin
  * O-step between the drifts (BAOAB) when gamma > 0, list rebuild whenever some
  * particle moved more than skin/2 since the last build, RBL force, final kick.
- * Synchronises at the end and reports device flags. */
+ * Between two steps the closing half kick of one and the opening half kick of the
+ * next are one kick of dt, also across calls: a call ends after its last force
+ * evaluation and the next call's first step applies the pending half kick with its
+ * own, so a run gives the same trajectory however it is split into calls.  The
+ * velocities that rbl_get_state, rbl_observables and checkpoints report or keep are
+ * those at the end of the last step (the pending half kick included in what is
+ * reported; a checkpoint keeps it pending).  rbl_set_charges and rbl_build_lists
+ * apply a pending half kick first (it is due with the current force); rbl_set_state
+ * discards it.  Synchronises at the end and reports device flags. */
 rbl_status rbl_step(rbl_ctx *ctx, int n);
 
 /* rbl_step without the wait: enqueues the n steps on the context's stream and returns.

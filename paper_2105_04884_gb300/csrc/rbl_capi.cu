@@ -398,6 +398,18 @@ rbl_status ensure_force(rbl_ctx *ctx, bool energy)
     return RBL_OK;
 }
 
+// Applies the half kick a step call left pending (before anything that changes the
+// force it is due with: charges, a forced rebuild).
+rbl_status resolve_kick(rbl_ctx *ctx)
+{
+    if (!ctx->kick_pending) return RBL_OK;
+    rbl_status st = ensure_force(ctx, false);
+    if (st != RBL_OK) return st;
+    CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+    ctx->kick_pending = 0;
+    return RBL_OK;
+}
+
 // Phases of a timed step: kick/drift/thermostat, cell sort chain, list build,
 // force kernel, force reduction.
 constexpr int kPhases = 5, kPhaseEvents = kPhases + 1;
@@ -440,17 +452,19 @@ rbl_status ensure_events(rbl_ctx *ctx, int steps)
 // rebuild chain, then the force and its reduction.  No host round trip and no
 // empty launches when no rebuild is due.
 // The captured steps.  Every step is kick(ck) + drift (+ O), the device-conditional
-// rebuild chain, the force at n + 1 and its reduction; the first step of a call
-// opens with a half kick, and the last one (energy estimates refreshed) ends with
-// the closing half kick, so a call of n >= 2 steps replays FIRST, MID^(n-2), LAST
-// and a call of one step SINGLE.
-enum StepGraph { kGraphMid = 0, kGraphFirst = 1, kGraphLast = 2, kGraphSingle = 3 };
+// rebuild chain, the force at n + 1 and its reduction.  A call's last step ends
+// after its force (with the energy estimates refreshed); its closing half kick is
+// left pending and applied by the next call's first step together with that step's
+// opening half kick, one kick of dt as between the steps inside a call, so the
+// trajectory does not depend on how a run is split into calls.  Only the first step
+// after a new state (nothing pending) opens with a half kick.
+enum StepGraph { kGraphMid = 0, kGraphFirst = 1, kGraphMidE = 2, kGraphFirstE = 3 };
 
 rbl_status ensure_graph(rbl_ctx *ctx, int kind)
 {
     if (ctx->graph_exec[kind]) return RBL_OK;
-    const bool half = kind == kGraphFirst || kind == kGraphSingle;
-    const bool last = kind == kGraphLast || kind == kGraphSingle;
+    const bool half = kind == kGraphFirst || kind == kGraphFirstE;
+    const bool last = kind == kGraphMidE || kind == kGraphFirstE;
     const double ck = half ? 0.5 * ctx->prm.dt : ctx->prm.dt;
     cudaStream_t s = ctx->stream;
     CK(launch_force_kernel(ctx->view, 1, last, s, true)); // kernel attributes, before the capture
@@ -479,7 +493,6 @@ rbl_status ensure_graph(rbl_ctx *ctx, int kind)
         if (ec == cudaSuccess)
             ec = cudaStreamUpdateCaptureDependencies(s, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (ec == cudaSuccess) ec = launch_forces(ctx->view, 1, 1, last, s);
-        if (ec == cudaSuccess && last) ec = launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, s);
         cudaGraph_t gout = nullptr;
         e = cudaStreamEndCapture(s, &gout);
         if (ec != cudaSuccess) e = ec;
@@ -659,6 +672,7 @@ rbl_status rbl_set_state(rbl_ctx *ctx, const double *x, const double *v, long lo
     ctx->lists_valid = 0;
     ctx->force_valid = 0;
     ctx->energy_valid = 0;
+    ctx->kick_pending = 0;
     if (!ptr_is_device) {
         rbl_status st = check_flags(ctx);
         if (st != RBL_OK) return st;
@@ -678,6 +692,8 @@ rbl_status rbl_set_charges(rbl_ctx *ctx, const double *q)
             set_err(ctx, "charge %lld is not finite", k);
             return RBL_EINVAL;
         }
+    rbl_status st = resolve_kick(ctx); // the pending half kick is due with the old charges' force
+    if (st != RBL_OK) return st;
     double *sq = ctx->view.staging;
     CK(cudaMemcpyAsync(sq, q, 8 * (size_t)ctx->n_real, cudaMemcpyHostToDevice, ctx->stream));
     CK(launch_set_charges(ctx->view, sq, ctx->stream));
@@ -693,12 +709,14 @@ rbl_status rbl_get_state(rbl_ctx *ctx, double *x, double *v, long long *step, in
     if (step) *step = ctx->step;
     if (!x && !v) return RBL_OK;
     size_t bytes = 24 * (size_t)ctx->n_real;
+    // velocities as of the end of the last step: with its closing half kick
+    const double ck = ctx->kick_pending ? 0.5 * ctx->prm.dt : 0.0;
     if (ptr_is_device) {
-        CK(launch_store_state(ctx->view, x, v, ctx->stream));
+        CK(launch_store_state(ctx->view, x, v, ctx->stream, ck));
         return RBL_OK;
     }
     double *sx = ctx->view.staging, *sv = ctx->view.staging + 3 * (size_t)ctx->n_real;
-    CK(launch_store_state(ctx->view, x ? sx : nullptr, v ? sv : nullptr, ctx->stream));
+    CK(launch_store_state(ctx->view, x ? sx : nullptr, v ? sv : nullptr, ctx->stream, ck));
     if (x) CK(cudaMemcpyAsync(x, sx, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     if (v) CK(cudaMemcpyAsync(v, sv, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -714,7 +732,8 @@ struct CkptHeader {
     int R;
     int precision;
     int lists_valid;        // the lists were built from the saved images
-    int reserved[3];
+    int kick_pending;       // the velocities still lack the last step's closing half kick
+    int reserved[2];
 };
 
 static size_t ckpt_head_bytes(int R) { return (sizeof(CkptHeader) + 8 * (size_t)R + 15) & ~(size_t)15; }
@@ -740,6 +759,7 @@ rbl_status rbl_save_checkpoint(rbl_ctx *ctx, void *buf, int ptr_is_device)
     hd.R = ctx->R;
     hd.precision = ctx->prm.precision;
     hd.lists_valid = ctx->lists_valid;
+    hd.kick_pending = ctx->kick_pending;
     std::memcpy(h.data(), &hd, sizeof(hd));
     for (int r = 0; r < ctx->R; ++r)
         std::memcpy(h.data() + sizeof(CkptHeader) + 8 * (size_t)r, &ctx->h_rs[r].n_rebuild, 8);
@@ -815,12 +835,15 @@ rbl_status rbl_load_checkpoint(rbl_ctx *ctx, const void *buf, int ptr_is_device)
     ctx->lists_valid = hd.lists_valid ? 1 : 0;
     ctx->force_valid = 0;
     ctx->energy_valid = 0;
+    ctx->kick_pending = hd.kick_pending ? 1 : 0; // the force it is due with is recomputed first
     return check_flags(ctx);
 }
 
 rbl_status rbl_build_lists(rbl_ctx *ctx)
 {
     if (!ctx) return RBL_EINVAL;
+    rbl_status st0 = resolve_kick(ctx); // due with the force of the current lists
+    if (st0 != RBL_OK) return st0;
     ctx->lists_valid = 0;
     rbl_status st = ensure_lists(ctx);
     if (st != RBL_OK) return st;
@@ -853,15 +876,15 @@ static rbl_status step_impl(rbl_ctx *ctx, int n, bool sync)
     if (n == 0) return RBL_OK;
     rbl_status st = ensure_force(ctx, false);
     if (st != RBL_OK) return st;
-    // first step: opening half kick; middle steps: the closing and opening half
-    // kicks fused into one kick of dt (graph replay); last step also refreshes the
-    // energy/virial estimates.
+    // every step kicks by dt (the previous step's closing half kick and its own
+    // opening one), except the first step after a new state, which opens with a half
+    // kick; the last step also refreshes the energy/virial estimates and leaves its
+    // closing half kick pending
+    const double dt = ctx->prm.dt, ck0 = ctx->kick_pending ? dt : 0.5 * dt;
     if (ctx->phase_timing) {
         st = ensure_events(ctx, n);
         if (st != RBL_OK) return st;
-        for (int k = 0; k < n; ++k)
-            CK(enqueue_step(ctx, k == 0 ? 0.5 * ctx->prm.dt : ctx->prm.dt, k == n - 1, ctx->ev + kPhaseEvents * k));
-        CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+        for (int k = 0; k < n; ++k) CK(enqueue_step(ctx, k == 0 ? ck0 : dt, k == n - 1, ctx->ev + kPhaseEvents * k));
         CK(cudaStreamSynchronize(ctx->stream));
         for (int k = 0; k < n; ++k)
             for (int ph = 0; ph < kPhases; ++ph) {
@@ -873,29 +896,30 @@ static rbl_status step_impl(rbl_ctx *ctx, int n, bool sync)
         ctx->step += n;
         ctx->force_valid = 1;
         ctx->energy_valid = 1;
+        ctx->kick_pending = 1;
         return check_flags(ctx);
     }
     if (ctx->stream == nullptr) {
         // the legacy default stream cannot be captured: launch directly
-        CK(enqueue_step(ctx, 0.5 * ctx->prm.dt, n == 1));
-        for (int k = 1; k < n - 1; ++k) CK(enqueue_step(ctx, ctx->prm.dt, false));
-        if (n > 1) CK(enqueue_step(ctx, ctx->prm.dt, true));
-        CK(launch_integrate(ctx->view, 0.5 * ctx->prm.dt, false, ctx->stream));
+        for (int k = 0; k < n; ++k) CK(enqueue_step(ctx, k == 0 ? ck0 : dt, k == n - 1));
     } else {
-        const int first = n == 1 ? kGraphSingle : kGraphFirst;
+        const bool p = ctx->kick_pending != 0;
+        const int first = n == 1 ? (p ? kGraphMidE : kGraphFirstE) : (p ? kGraphMid : kGraphFirst);
         st = ensure_graph(ctx, first);
         if (st == RBL_OK && n > 2) st = ensure_graph(ctx, kGraphMid);
-        if (st == RBL_OK && n > 1) st = ensure_graph(ctx, kGraphLast);
+        if (st == RBL_OK && n > 1) st = ensure_graph(ctx, kGraphMidE);
         if (st != RBL_OK) return st;
         CK(cudaGraphLaunch(ctx->graph_exec[first], ctx->stream));
         for (int k = 1; k < n - 1; ++k) CK(cudaGraphLaunch(ctx->graph_exec[kGraphMid], ctx->stream));
-        if (n > 1) CK(cudaGraphLaunch(ctx->graph_exec[kGraphLast], ctx->stream));
+        if (n > 1) CK(cudaGraphLaunch(ctx->graph_exec[kGraphMidE], ctx->stream));
     }
     ctx->step += n;
     ctx->force_valid = 1;
     ctx->energy_valid = 1;
+    ctx->kick_pending = 1;
     return sync ? check_flags(ctx) : RBL_OK;
 }
+
 
 rbl_status rbl_step(rbl_ctx *ctx, int n) { return step_impl(ctx, n, true); }
 
@@ -912,7 +936,7 @@ rbl_status enqueue_observables(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
 {
     rbl_status st = ensure_force(ctx, true);
     if (st != RBL_OK) return st;
-    CK(launch_kinetic(ctx->view, ctx->stream));
+    CK(launch_kinetic(ctx->view, ctx->stream, ctx->kick_pending ? 0.5 * ctx->prm.dt : 0.0));
     // page-locked host memory (mapped into the device's address space) and device
     // memory are written by the kernel itself; anything else through the staging area
     void *direct = ptr_is_device ? (void *)out : nullptr;

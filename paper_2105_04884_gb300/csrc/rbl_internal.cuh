@@ -594,6 +594,7 @@ struct rbl_ctx {
     int lists_valid;   // lists match the current positions
     int force_valid;   // F matches the current positions and step counter
     int energy_valid;  // energy/virial estimates match F
+    int kick_pending;  // the last step call's closing half kick (dt/2 F) is not applied yet
     long long step;    // host mirror of the step counter
     size_t staging_bytes;
     cudaGraphExec_t graph_exec[4]; // captured steps: middle, first, last, single (enum StepGraph)
@@ -613,7 +614,9 @@ struct rbl_ctx {
 // Kernel launchers implemented in the .cu files.
 namespace rbl {
 cudaError_t launch_load_state(const View &v, const double *x, const double *vel, cudaStream_t s);
-cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s);
+// ck: a half kick still pending at the end of a step call, applied to the velocities
+// written (or summed) but not to the state
+cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s, double ck = 0.0);
 cudaError_t launch_store_images(const View &v, unsigned *img, cudaStream_t s);
 cudaError_t launch_load_images(const View &v, const unsigned *img, cudaStream_t s);
 cudaError_t launch_requantize(const View &v, cudaStream_t s);
@@ -630,7 +633,7 @@ cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s);
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
-cudaError_t launch_kinetic(const View &v, cudaStream_t s);
+cudaError_t launch_kinetic(const View &v, cudaStream_t s, double ck = 0.0);
 cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);

@@ -85,8 +85,31 @@ __global__ void k_set_charges(View v, const double *q)
     v.q32[i] = __double2float_rn(qi);
 }
 
-// SoA cell-ordered state -> packed AoS tag-ordered output.
-__global__ void k_store(View v, double *x, double *vel)
+// Velocity component a of slot i after a kick of ck by the corrected force (ck 0:
+// no kick).  FP32 path: the corrected force is the integer q_i - m - [tag < r] (the
+// net force removed exactly, see k_force_finish), converted exactly and applied with
+// one fused multiply-add, v + (ck 2^-24) (q_i - m - [tag < r]); FP64 path:
+// v + ck (F - F_cor).  k_integrate kicks with these same operations, so a kick
+// computed here for output equals the one the next step applies.
+template <bool FP32>
+__device__ __forceinline__ double kick_v(const View &v, const RepScalars *rsc, int i, int tag, int a, double ck,
+                                         double cks)
+{
+    const size_t N = (size_t)v.N;
+    const double va = v.v[a * N + i];
+    if (ck == 0.0) return va;
+    if (FP32) {
+        const long long q = ((const long long *)v.F)[a * N + i] - rsc->fcor_q[a] - (tag < rsc->fcor_r[a] ? 1 : 0);
+        return fma(cks, i64_to_double(q), va);
+    }
+    return fma(ck, ((const double *)v.F)[a * N + i] - rsc->fcor[a], va);
+}
+
+// SoA cell-ordered state -> packed AoS tag-ordered output; ck: the half kick still
+// pending at the end of a step call, applied to the velocities written (the state
+// keeps them unkicked).
+template <bool FP32>
+__global__ void k_store(View v, double *x, double *vel, double ck, double cks)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.N) return;
@@ -94,11 +117,12 @@ __global__ void k_store(View v, double *x, double *vel)
     bool live;
     const int r = slot_replica(v, i, live);
     if (!live) return;
-    size_t t = (size_t)v.box[r].in0 + (size_t)v.tag[i];
+    const int tag = v.tag[i];
+    size_t t = (size_t)v.box[r].in0 + (size_t)tag;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (x) x[t * 3 + a] = v.x[a * N + i];
-        if (vel) vel[t * 3 + a] = v.v[a * N + i];
+        if (vel) vel[t * 3 + a] = kick_v<FP32>(v, v.rs + r, i, tag, a, ck, cks);
     }
 }
 
@@ -166,14 +190,7 @@ __global__ void __launch_bounds__(kBlock) k_integrate(View v, double ck, double 
     const int tag = v.tag[i];
     double vv[3], xx[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (FP32) {
-            const long long q = ((const long long *)v.F)[a * N + i] - rsc->fcor_q[a] - (tag < rsc->fcor_r[a] ? 1 : 0);
-            vv[a] = fma(cks, i64_to_double(q), v.v[a * N + i]);
-        } else {
-            vv[a] = fma(ck, ((const double *)v.F)[a * N + i] - rsc->fcor[a], v.v[a * N + i]);
-        }
-    }
+    for (int a = 0; a < 3; ++a) vv[a] = kick_v<FP32>(v, rsc, i, tag, a, ck, cks);
     if constexpr (!DRIFT) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) v.v[a * N + i] = vv[a];
@@ -240,18 +257,24 @@ __device__ __forceinline__ T wsum(T x)
 // sum v^2 and sum v per tile (256 slots): one warp per tile, each lane summing its
 // 8 slots in order before one fixed shuffle tree, so the FP64 tree is paid once
 // per 256 particles; per-tile partials in staging, reduced per replica in a fixed
-// order by k_kinetic_finish.  Padding slots hold v = 0.
-__global__ void __launch_bounds__(32) k_kinetic(View v)
+// order by k_kinetic_finish.  Padding slots count as v = 0.  ck: the half kick still
+// pending at the end of a step call (the sums are of the kicked velocities).
+template <bool FP32>
+__global__ void __launch_bounds__(32) k_kinetic(View v, double ck, double cks)
 {
     const size_t N = (size_t)v.N;
     const size_t base = (size_t)blockIdx.x * kTile + threadIdx.x;
+    const int2 tl = v.tile[blockIdx.x];
+    const RepScalars *rsc = v.rs + tl.x;
     double x[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < kTile / 32; ++k) {
         const size_t i = base + (size_t)k * 32;
+        const bool live = (long long)i < (long long)tl.y;
+        const int tag = live && ck != 0.0 ? v.tag[i] : 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double va = v.v[a * N + i];
+            const double va = live ? kick_v<FP32>(v, rsc, (int)i, tag, a, ck, cks) : 0.0;
             x[0] = fma(va, va, x[0]);
             x[1 + a] += va;
         }
@@ -369,9 +392,10 @@ cudaError_t launch_requantize(const View &v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s)
+cudaError_t launch_store_state(const View &v, double *x, double *vel, cudaStream_t s, double ck)
 {
-    k_store<<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel);
+    if (v.precision == RBL_FP32) k_store<true><<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel, ck, ck * kFixedInv);
+    else k_store<false><<<ceil_div(v.N, kBlock), kBlock, 0, s>>>(v, x, vel, ck, ck * kFixedInv);
     return cudaGetLastError();
 }
 
@@ -436,9 +460,10 @@ cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic(const View &v, cudaStream_t s)
+cudaError_t launch_kinetic(const View &v, cudaStream_t s, double ck)
 {
-    k_kinetic<<<v.ntile, 32, 0, s>>>(v);
+    if (v.precision == RBL_FP32) k_kinetic<true><<<v.ntile, 32, 0, s>>>(v, ck, ck * kFixedInv);
+    else k_kinetic<false><<<v.ntile, 32, 0, s>>>(v, ck, ck * kFixedInv);
     k_kinetic_finish<<<v.R, kBlock, 0, s>>>(v);
     return cudaGetLastError();
 }

@@ -3,9 +3,12 @@
 Algorithm 1 draws each step's batches from the rows of the last list build with
 random numbers keyed by (seed, step, tag), so a resumed run reproduces the
 uninterrupted one only if it resumes with those rows.  A checkpoint carries the
-images the lists were built from; the tests run n + n steps in one context against
-n steps, a checkpoint, a new context that loads it, and n more steps, and require
-positions, velocities, step counter and rebuild counts to be bit-identical."""
+images the lists were built from; the tests run 2n steps in one call against n
+steps, a checkpoint, a new context that loads it, and n more steps, and require
+positions, velocities, step counter and rebuild counts to be bit-identical.  The
+same holds for a run split into calls in one context, with observations between
+them: a call leaves its last closing half kick pending for the next call's first
+step, as between the steps inside a call."""
 import numpy as np
 import pytest
 
@@ -43,11 +46,10 @@ def _rebuilds(ctx):
 
 
 def _check_resume(make, n, device):
-    # the reference continues its own context with the same calls: inside one call
-    # the closing and opening half kicks of consecutive steps are one kick of dt
+    # the reference runs the 2n steps in one call (a run's trajectory does not depend
+    # on how it is split into calls)
     ref = make()
-    ref.step(n)
-    ref.step(n)
+    ref.step(2 * n)
     x_ref, v_ref, step_ref = ref.get_state()
     nr_ref = _rebuilds(ref)
     assert nr_ref[0] >= 4  # the segment crosses several rebuilds
@@ -112,3 +114,49 @@ def test_checkpoint_of_other_sizes_rejected():
     c = _system(rbl.RBL_FP64, N=2000)()
     with pytest.raises(rbl.RblError):
         c.load_checkpoint(buf)
+
+
+@pytest.mark.parametrize("precision", [rbl.RBL_FP32, rbl.RBL_FP64])
+def test_call_splitting_does_not_change_the_trajectory(precision):
+    make = _system(precision, N=2000, seed=13)
+    a = make()
+    a.step(24)
+    b = make()  # split, with state and observables read in between
+    b.step(10)
+    b.get_state()
+    b.observables()
+    b.step(13)
+    b.get_state()
+    b.step(1)
+    c = make()  # one step per call, as an end-to-end loop runs
+    for _ in range(24):
+        c.step_async(1)
+        c.observables()
+    xa, va, sa = a.get_state()
+    for other in (b, c):
+        x, v, st = other.get_state()
+        assert st == sa
+        assert np.array_equal(x, xa) and np.array_equal(v, va)
+        assert _rebuilds(other) == _rebuilds(a)
+    assert a.observables()["K"] == c.observables()["K"]
+
+
+def test_pending_kick_applied_before_charges_change():
+    """rbl_set_charges applies the pending half kick with the force it is due with
+    (the old charges'), so setting the same charges again changes nothing."""
+    N, seed = 1500, 14
+    x, L = inputs.fcc(N, 0.8, 0.05, seed=seed)
+    v = inputs.maxwell_boltzmann(N, 1.5, seed=seed)
+    q = inputs.charges(N, 1.0, seed=seed)
+    args = dict(T=1.5, seed=seed, potential=rbl.RBL_POT_LJ_EWALD, alpha=1.0, charges=q, **SHARED)
+    a = rbl.System(x, v, L, **args)
+    a.step(12)
+    b = rbl.System(x, v, L, **args)
+    b.step(6)
+    b.set_charges(q)
+    b.step(6)
+    xa, va, _ = a.get_state()
+    xb, vb, _ = b.get_state()
+    # the kick is applied separately (two roundings instead of one fused kick of dt),
+    # so the trajectories agree to rounding, not bit for bit
+    assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-9
