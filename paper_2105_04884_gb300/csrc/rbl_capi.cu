@@ -25,10 +25,6 @@ namespace {
 const double kPi = 3.14159265358979323846264338327950288;
 constexpr long long kMaxSlots = 1ll << 30;  // particle slots of a context (int indices, int32 rows)
 
-// Byte offset of the rbl_obs[R] area in the staging buffer: after the kinetic
-// partials (4 doubles per tile).
-size_t obs_staging_offset(int ntile) { return ((size_t)ntile * 32 + 255) & ~(size_t)255; }
-
 // Sizes and offsets of every array of a context's workspace.
 struct Plan {
     size_t off[40];
@@ -189,8 +185,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
     const size_t Nq = p->potential == RBL_POT_LJ_EWALD ? Nz : 0; // charges only with the Ewald term
     size_t st = 64 * (size_t)n_real + 4096;            // packed x, v and images (host copies, checkpoints)
     if (st < 4 * Nz * (size_t)(p->p + 1)) st = 4 * Nz * (size_t)(p->p + 1); // batch hook
-    if (st < obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R)       // kinetic partials, then rbl_obs[R]
-        st = obs_staging_offset(P.ntile) + sizeof(rbl_obs) * (size_t)R;
+    if (st < sizeof(rbl_obs) * (size_t)R) st = sizeof(rbl_obs) * (size_t)R;   // rbl_obs[R]
     if (st < (1u << 20)) st = 1u << 20;
     P.staging_bytes = st;
     const size_t sizes[] = {
@@ -213,6 +208,7 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
         sizeof(RepScalars) * (size_t)R,             // rs
         sizeof(DevScalars),                         // sc
         P.staging_bytes,                            // staging
+        64 * (size_t)round_up(R, 16),               // kin_acc [8][R rounded up to 16]
         8 * Nq, 4 * Nq, 8 * Nq,                     // q, q32, q_in
     };
     P.n = (int)(sizeof(sizes) / sizeof(sizes[0]));
@@ -250,6 +246,16 @@ Box make_box(const rbl_params *p, int N, int first, int c0, int in0)
     b.c0 = c0;
     b.ncell = g.ncell;
     b.S = g.S;
+    // rbl_obs constants (host arithmetic without contraction: each operation rounded once)
+    const double n = (double)N, rs = p->r_s;
+    b.V = (b.L[0] * b.L[1]) * b.L[2];
+    b.n3 = 3.0 * n;
+    b.rho = n / b.V;
+    b.V3 = 3.0 * b.V;
+    const double i3 = 1.0 / ((rs * rs) * rs);
+    const double i9 = (i3 * i3) * i3;
+    b.U_tail = (((8.0 / 3.0) * kPi) * b.rho) * (i9 / 3.0 - i3);
+    b.P_tail = ((((16.0 / 3.0) * kPi) * b.rho) * b.rho) * ((2.0 * i9) / 3.0 - i3);
     return b;
 }
 
@@ -323,6 +329,8 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.rs = (RepScalars *)(base + P.off[k++]);
     v.sc = (DevScalars *)(base + P.off[k++]);
     v.staging = (double *)(base + P.off[k++]);
+    v.kin_acc = (unsigned long long *)(base + P.off[k++]);
+    v.kin_stride = round_up(P.R, 16);
     if (prm->potential == RBL_POT_LJ_EWALD) {
         v.q = (double *)(base + P.off[k++]);
         v.q32 = (float *)(base + P.off[k++]);
@@ -588,6 +596,7 @@ rbl_status create_impl(const rbl_params *prm, int R, const int *Ns, void *worksp
         e = cudaMemcpyAsync((void *)v.cell_rep, ctx->h_cell_rep, 4 * (size_t)P.ncell, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.sc, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.rs, 0, sizeof(RepScalars) * (size_t)R, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.kin_acc, 0, 64 * (size_t)v.kin_stride, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.F, 0, 24 * (size_t)P.N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.partials, 0, 64 * ((size_t)P.N / kMinBlock), s);
     if (e == cudaSuccess && v.q) {
@@ -930,13 +939,13 @@ rbl_status rbl_step_async(rbl_ctx *ctx, int n)
 }
 
 
-// Enqueues the kinetic sums, the device-side assembly of rbl_obs[R] (after the
-// kinetic partials in the staging area) and its copy to out.
+// Enqueues the observables launch (kinetic sums and the device-side assembly of
+// rbl_obs[R]) and, where out is not written by the kernel itself, its copy to out.
 rbl_status enqueue_observables(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
 {
     rbl_status st = ensure_force(ctx, true);
     if (st != RBL_OK) return st;
-    CK(launch_kinetic(ctx->view, ctx->stream, ctx->kick_pending ? 0.5 * ctx->prm.dt : 0.0));
+    const double ck = ctx->kick_pending ? 0.5 * ctx->prm.dt : 0.0;
     // page-locked host memory (mapped into the device's address space) and device
     // memory are written by the kernel itself; anything else through the staging area
     void *direct = ptr_is_device ? (void *)out : nullptr;
@@ -947,11 +956,11 @@ rbl_status enqueue_observables(rbl_ctx *ctx, rbl_obs *out, int ptr_is_device)
         cudaGetLastError(); // an unregistered pointer is not an error here
     }
     if (direct) {
-        CK(launch_obs(ctx->view, (rbl_obs *)direct, ctx->prm.r_s, ctx->stream));
+        CK(launch_observables(ctx->view, (rbl_obs *)direct, ck, ctx->stream));
         return RBL_OK;
     }
-    rbl_obs *dev = (rbl_obs *)((char *)ctx->view.staging + obs_staging_offset(ctx->view.ntile));
-    CK(launch_obs(ctx->view, dev, ctx->prm.r_s, ctx->stream));
+    rbl_obs *dev = (rbl_obs *)ctx->view.staging;
+    CK(launch_observables(ctx->view, dev, ck, ctx->stream));
     CK(cudaMemcpyAsync(out, dev, sizeof(rbl_obs) * (size_t)ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
     return RBL_OK;
 }

@@ -225,7 +225,7 @@ static_assert(kMaskStage > 0 && (kMaskStage & (kMaskStage - 1)) == 0 && kMaskSta
 template <int MODE, bool ENERGY, bool EWALD>
 struct ForceTuning {
     static constexpr int gather = MODE == 1 ? 8 : (MODE == 3 ? (EWALD ? 8 : 12) : 4);
-    static constexpr int regs = (MODE == 1 || MODE == 3) ? 80 : (ENERGY ? 72 : 64);
+    static constexpr int regs = (MODE == 1 || MODE == 3) ? 80 : 64;
 };
 
 template <int MODE, bool FP32, bool ENERGY, int PMAX, bool EWALD>

@@ -40,6 +40,8 @@ struct DevScalars {
     unsigned flags;                 // kFlag* bits
     int rebuild;                    // 1 when some replica must rebuild before the next force
     unsigned long long step;        // step counter n (batch/noise counters), shared by all replicas
+    unsigned obs_ticket;            // blocks of the observables launch done so far (zero between launches)
+    unsigned pad_;
 };
 
 // Per-replica scalars living in device memory ([R] in the workspace).
@@ -52,8 +54,6 @@ struct RepScalars {
     long long fcor_r[3];            // 0 <= fcor_r < N; tags < fcor_r subtract fcor_q + 1, the rest fcor_q
     double energy, virial;          // RBL estimates from the last evaluation
     double u_exact, w_exact;        // unsampled energy and virial (on demand)
-    double ksum;                    // sum v^2 (on demand)
-    double psum[3];                 // sum v (on demand)
     int rebuild;                    // 1 when this replica's lists must be rebuilt
     int nc_max, ns_max;             // longest rows at the last build (even past capacity)
     int m_max;                      // largest stencil population at the last build
@@ -79,6 +79,9 @@ struct Box {
     int c0, ncell;                  // cells [c0, c0 + ncell); c0 + ncell is the pad cell
     int n[3], nofs[3], ofs[3][kMaxStencil];
     int S;                          // segments per home cell (nofs_y * nofs_z)
+    // rbl_obs constants of the replica, each rounded as written: 3N, V = (L_x L_y) L_z,
+    // rho = N / V, 3V and the LJ tail terms at r_s (Sec. 3)
+    double n3, V, rho, V3, U_tail, P_tail;
 };
 
 // Kernel-visible view of a context (passed by value).
@@ -140,6 +143,10 @@ struct View {
     RepScalars *rs;                 // [R]
     DevScalars *sc;
     double *staging;                // host/device I/O scratch
+    unsigned long long *kin_acc;    // [8][kin_stride]: observables launch, replica r's sums of v^2,
+                                    // v_x, v_y, v_z as (integer part, fraction in units of 2^-40), each
+                                    // summed over tiles (mod 2^64); zero between launches
+    int kin_stride;                 // R rounded up to 16 (one 128-byte line per value and 16 replicas)
 };
 
 // Replica of particle slot i (i < N) and whether the slot holds a particle.
@@ -524,13 +531,6 @@ struct FixedAcc {
 constexpr double kFixedScale = 16777216.0;          // 2^24
 constexpr double kFixedInv = 1.0 / 16777216.0;
 
-// int64 -> double for |q| < 2^51 without the FP64 conversion unit: place q in the
-// mantissa of 1.5 * 2^52 and subtract that constant.
-__device__ __forceinline__ double i64_to_double(long long q)
-{
-    return __longlong_as_double(q + 0x4338000000000000LL) - 6755399441055744.0;
-}
-
 // binary32 -> FP64 by bit manipulation (normal numbers and zero; subnormals -> 0).
 __device__ __forceinline__ double f32_to_double(float f)
 {
@@ -633,8 +633,7 @@ cudaError_t launch_init_single(const View &v, const Box &b, cudaStream_t s);
 cudaError_t launch_exact_energy(const View &v, cudaStream_t s);
 cudaError_t launch_store_forces(const View &v, double *F, cudaStream_t s);
 cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t s);
-cudaError_t launch_kinetic(const View &v, cudaStream_t s, double ck = 0.0);
-cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s);
+cudaError_t launch_observables(const View &v, rbl_obs *out, double ck, cudaStream_t s);
 cudaError_t launch_batch(const View &v, unsigned long long step, int *out_j, int *out_n, cudaStream_t s);
 cudaError_t launch_rdf(const View &v, float dr, int nbins, unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_profile(const View &v, int axis, int nbins, unsigned long long *hist, cudaStream_t s);

@@ -89,8 +89,9 @@ __global__ void k_set_charges(View v, const double *q)
 // no kick).  FP32 path: the corrected force is the integer q_i - m - [tag < r] (the
 // net force removed exactly, see k_force_finish), converted exactly and applied with
 // one fused multiply-add, v + (ck 2^-24) (q_i - m - [tag < r]); FP64 path:
-// v + ck (F - F_cor).  k_integrate kicks with these same operations, so a kick
-// computed here for output equals the one the next step applies.
+// v + ck (F - F_cor).  k_integrate kicks with these same operations (ck = dt when
+// it applies a pending closing half kick together with its own opening one); the
+// velocities reported between steps are this with ck = dt/2.
 template <bool FP32>
 __device__ __forceinline__ double kick_v(const View &v, const RepScalars *rsc, int i, int tag, int a, double ck,
                                          double cks)
@@ -100,7 +101,7 @@ __device__ __forceinline__ double kick_v(const View &v, const RepScalars *rsc, i
     if (ck == 0.0) return va;
     if (FP32) {
         const long long q = ((const long long *)v.F)[a * N + i] - rsc->fcor_q[a] - (tag < rsc->fcor_r[a] ? 1 : 0);
-        return fma(cks, i64_to_double(q), va);
+        return fma(cks, __ll2double_rn(q), va); // exact: |q| < 2^53 (force range check)
     }
     return fma(ck, ((const double *)v.F)[a * N + i] - rsc->fcor[a], va);
 }
@@ -254,63 +255,137 @@ __device__ __forceinline__ T wsum(T x)
     return x;
 }
 
-// sum v^2 and sum v per tile (256 slots): one warp per tile, each lane summing its
-// 8 slots in order before one fixed shuffle tree, so the FP64 tree is paid once
-// per 256 particles; per-tile partials in staging, reduced per replica in a fixed
-// order by k_kinetic_finish.  Padding slots count as v = 0.  ck: the half kick still
-// pending at the end of a step call (the sums are of the kicked velocities).
-template <bool FP32>
-__global__ void __launch_bounds__(32) k_kinetic(View v, double ck, double cks)
-{
-    const size_t N = (size_t)v.N;
-    const size_t base = (size_t)blockIdx.x * kTile + threadIdx.x;
-    const int2 tl = v.tile[blockIdx.x];
-    const RepScalars *rsc = v.rs + tl.x;
-    double x[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < kTile / 32; ++k) {
-        const size_t i = base + (size_t)k * 32;
-        const bool live = (long long)i < (long long)tl.y;
-        const int tag = live && ck != 0.0 ? v.tag[i] : 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double va = live ? kick_v<FP32>(v, rsc, (int)i, tag, a, ck, cks) : 0.0;
-            x[0] = fma(va, va, x[0]);
-            x[1 + a] += va;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = wsum(x[k]);
-    if (threadIdx.x < 4) {
-        const double out = threadIdx.x == 0 ? x[0] : threadIdx.x == 1 ? x[1] : threadIdx.x == 2 ? x[2] : x[3];
-        v.staging[(size_t)blockIdx.x * 4 + threadIdx.x] = out;
-    }
-}
+// Observables launch, part 1: the kinetic sums of one tile (256 slots) per warp.
+// Each lane sums its 8 slots in order; the four per-lane sums (v^2, v_x, v_y, v_z) are
+// then reduced over the warp by one fixed transposed shuffle tree (6 FP64 additions
+// per lane instead of 20: the first level halves the values a lane carries, the
+// second halves them again), after which lanes 8k hold the tile's sum of value k.
+// ck: the half kick still pending at the end of a step call (the sums are of the
+// kicked velocities).  Padding slots count as v = 0.  Each tile sum s is split
+// exactly into floor(s) and the fraction s - floor(s) rounded to a multiple of 2^-40,
+// both integers, and the replica's totals of those integers are accumulated by
+// integer atomics: exact and order-free, so the result depends on the replica's
+// tiles alone, never on the launch shape or on the other replicas of an ensemble.
+// Part 2 (the block that finishes last) turns each replica's totals into one
+// correctly rounded FP64 value and assembles rbl_obs.
+constexpr int kObsBlock = 128;
+constexpr double kTwo40 = 1099511627776.0;       // 2^40
+constexpr double kKinRange = 4503599627370496.0; // 2^52: a tile sum beyond it is not split exactly
 
-__global__ void __launch_bounds__(kBlock) k_kinetic_finish(View v)
+template <bool FP32>
+__global__ void __launch_bounds__(kObsBlock) k_observables(View v, double ck, double cks, rbl_obs *out)
 {
-    __shared__ double sh[4][kBlock / 32];
-    const Box &bx = v.box[blockIdx.x];
-    const int t0 = bx.first >> kTileShift, nt = bx.slots >> kTileShift;
-    double acc[4] = {0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nt; b += blockDim.x)
+    constexpr int kWarps = kObsBlock / 32;
+    __shared__ long long s_q[kWarps][8];
+    __shared__ int s_rep[kWarps];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tile = blockIdx.x * kWarps + wid;
+    if (tile < v.ntile) {
+        const size_t base = (size_t)tile * kTile + lane;
+        const int2 tl = v.tile[tile];
+        const RepScalars *rsc = v.rs + tl.x;
+        double x[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += v.staging[(size_t)(t0 + b) * 4 + k];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int k = 0; k < kTile / 32; ++k) {
+            const size_t i = base + (size_t)k * 32;
+            const bool live = (long long)i < (long long)tl.y;
+            const int tag = live && ck != 0.0 ? v.tag[i] : 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        double s = wsum(acc[k]);
-        if (lane == 0) sh[k][wid] = s;
+            for (int a = 0; a < 3; ++a) {
+                const double va = live ? kick_v<FP32>(v, rsc, (int)i, tag, a, ck, cks) : 0.0;
+                x[0] = fma(va, va, x[0]);
+                x[1 + a] += va;
+            }
+        }
+        // level 16: lanes below 16 keep values 0, 1, the others 2, 3
+        const bool u16 = (lane & 16) != 0;
+        double a0 = u16 ? x[2] : x[0], a1 = u16 ? x[3] : x[1];
+        const double o0 = u16 ? x[0] : x[2], o1 = u16 ? x[1] : x[3];
+        a0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+        a1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+        // level 8: one value per lane, value 2 [lane & 16] + [lane & 8]
+        const bool u8 = (lane & 8) != 0;
+        double t = u8 ? a1 : a0;
+        t += __shfl_xor_sync(0xffffffffu, u8 ? a0 : a1, 8);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if ((lane & 7) == 0) {
+            const int k = lane >> 3;
+            long long qi = 0, qf = 0;
+            if (fabs(t) < kKinRange) {
+                const double fl = floor(t);
+                qi = (long long)fl;                      // exact: |fl| < 2^52
+                qf = __double2ll_rn((t - fl) * kTwo40);  // t - fl exact, in [0, 1)
+            } else {
+                atomicOr(&v.sc->flags, kFlagNonFinite); // non-finite or absurd velocities
+            }
+            s_q[wid][2 * k] = qi;
+            s_q[wid][2 * k + 1] = qf;
+        }
+        if (lane == 0) s_rep[wid] = tl.x;
+    } else if (lane == 0) {
+        s_rep[wid] = -1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot[4] = {0, 0, 0, 0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int k = 0; k < 4; ++k) tot[k] += sh[k][w];
-        RepScalars &rsc = v.rs[blockIdx.x];
-        rsc.ksum = tot[0];
-        for (int a = 0; a < 3; ++a) rsc.psum[a] = tot[1 + a];
+    // one atomic per value for each run of this block's warps in the same replica
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x;
+        unsigned long long *acc_k = v.kin_acc + (size_t)k * v.kin_stride;
+        int rep = -1;
+        long long acc = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (s_rep[w] < 0) break;
+            if (s_rep[w] != rep) {
+                if (rep >= 0) atomicAdd(acc_k + rep, (unsigned long long)acc);
+                rep = s_rep[w];
+                acc = 0;
+            }
+            acc += s_q[w][k];
+        }
+        if (rep >= 0) atomicAdd(acc_k + rep, (unsigned long long)acc);
+        __threadfence();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&v.sc->obs_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // part 2: every block's totals are in; read and clear them
+    __threadfence();
+    for (int r = threadIdx.x; r < v.R; r += blockDim.x) {
+        unsigned long long q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = atomicExch(v.kin_acc + (size_t)k * v.kin_stride + r, 0ull);
+        double tot[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long qi = (long long)q[2 * k], qf = (long long)q[2 * k + 1];
+            // exact integer part and exact fraction (< 1), one rounding in the add
+            tot[k] = __dadd_rn((double)(qi + (qf >> 40)), __dmul_rn((double)(qf & ((1ll << 40) - 1)), 1.0 / kTwo40));
+        }
+        const RepScalars &s = v.rs[r];
+        const Box &b = v.box[r];
+        const double T_kin = __ddiv_rn(tot[0], b.n3);
+        rbl_obs &o = out[r]; // written field by field (out may be mapped host memory)
+        o.U_est = s.energy;
+        o.W_est = s.virial;
+        o.K = __dmul_rn(0.5, tot[0]);
+        o.T_kin = T_kin;
+        o.P = __dadd_rn(__dmul_rn(b.rho, T_kin), __ddiv_rn(s.virial, b.V3));
+        o.U_tail = b.U_tail;
+        o.P_tail = b.P_tail;
+        for (int a = 0; a < 3; ++a) o.net_momentum[a] = tot[1 + a];
+        o.step = (long long)v.sc->step;
+        o.n_rebuild = s.n_rebuild;
+        const double n = (double)b.N;
+        o.Ns_mean = __ddiv_rn((double)s.ns_sum, n);
+        o.Nc_mean = __ddiv_rn((double)s.nc_sum, n);
+        o.Mc_mean = __ddiv_rn((double)s.m_sum, n);
+        o.Ns_max = s.ns_max;
+        o.Nc_max = s.nc_max;
+    }
+    if (threadIdx.x == 0) v.sc->obs_ticket = 0u;
 }
 
 // Density profile along one axis (Sec. 3 observables): particle counts in nbins
@@ -418,53 +493,11 @@ cudaError_t launch_integrate(const View &v, double ck, bool drift, cudaStream_t 
     return cudaGetLastError();
 }
 
-// rbl_obs of every replica from its scalars (kinetic sums, energy and virial of the
-// last force evaluation, list statistics): out[R], for rbl_observables and its
-// asynchronous form alike.  Explicitly rounded operations, no contraction.
-__global__ void k_obs(View v, rbl_obs *out, double rs)
+cudaError_t launch_observables(const View &v, rbl_obs *out, double ck, cudaStream_t s)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= v.R) return;
-    const double pi = 3.14159265358979323846;
-    const RepScalars &s = v.rs[r];
-    const Box &b = v.box[r];
-    const double n = (double)b.N;
-    const double V = __dmul_rn(__dmul_rn(b.L[0], b.L[1]), b.L[2]);
-    const double rho = __ddiv_rn(n, V);
-    const double i3 = __ddiv_rn(1.0, __dmul_rn(__dmul_rn(rs, rs), rs));
-    const double i9 = __dmul_rn(__dmul_rn(i3, i3), i3);
-    rbl_obs o;
-    o.U_est = s.energy;
-    o.W_est = s.virial;
-    o.K = __dmul_rn(0.5, s.ksum);
-    o.T_kin = __ddiv_rn(s.ksum, __dmul_rn(3.0, n));
-    o.P = __dadd_rn(__dmul_rn(rho, o.T_kin), __ddiv_rn(s.virial, __dmul_rn(3.0, V)));
-    // per-particle energy and pressure tails of the truncated LJ fluid (Sec. 3)
-    o.U_tail = __dmul_rn(__dmul_rn(__dmul_rn(__ddiv_rn(8.0, 3.0), pi), rho), __dsub_rn(__ddiv_rn(i9, 3.0), i3));
-    o.P_tail = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__ddiv_rn(16.0, 3.0), pi), rho), rho),
-                         __dsub_rn(__ddiv_rn(__dmul_rn(2.0, i9), 3.0), i3));
-    for (int a = 0; a < 3; ++a) o.net_momentum[a] = s.psum[a];
-    o.step = (long long)v.sc->step;
-    o.n_rebuild = s.n_rebuild;
-    o.Ns_mean = __ddiv_rn((double)s.ns_sum, n);
-    o.Nc_mean = __ddiv_rn((double)s.nc_sum, n);
-    o.Mc_mean = __ddiv_rn((double)s.m_sum, n);
-    o.Ns_max = s.ns_max;
-    o.Nc_max = s.nc_max;
-    out[r] = o;
-}
-
-cudaError_t launch_obs(const View &v, rbl_obs *out, double rs, cudaStream_t s)
-{
-    k_obs<<<ceil_div(v.R, 128), 128, 0, s>>>(v, out, rs);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_kinetic(const View &v, cudaStream_t s, double ck)
-{
-    if (v.precision == RBL_FP32) k_kinetic<true><<<v.ntile, 32, 0, s>>>(v, ck, ck * kFixedInv);
-    else k_kinetic<false><<<v.ntile, 32, 0, s>>>(v, ck, ck * kFixedInv);
-    k_kinetic_finish<<<v.R, kBlock, 0, s>>>(v);
+    const int g = ceil_div(v.ntile, kObsBlock / 32);
+    if (v.precision == RBL_FP32) k_observables<true><<<g, kObsBlock, 0, s>>>(v, ck, ck * kFixedInv, out);
+    else k_observables<false><<<g, kObsBlock, 0, s>>>(v, ck, ck * kFixedInv, out);
     return cudaGetLastError();
 }
 
