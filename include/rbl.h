@@ -109,8 +109,10 @@ typedef struct {
     int subtract_net_force; /* 1 (default): subtract the mean force (Appendix A) */
     int cells_per_cutoff; /* K: cell width >= (r_s + skin)/K, stencil (2K+1)^3; 1..3 */
     int cap_core;         /* core row capacity; 0 = derived from the density */
-    int cap_stencil;      /* largest stencil population of a cell (shell/full rows are
-                             bitmasks over it); 0 = derived from the density */
+    int cap_stencil;      /* capacity of a cell's culled candidate table (shell
+                             sampling: the stencil members within r_s + skin of the
+                             cell's particles; shell rows are bitmasks over it);
+                             0 = derived from the density */
     double rho_cap;       /* number density the derived capacities are sized for;
                              0 = the mean density N/V.  Set it to the densest
                              region's density for inhomogeneous systems (a liquid
@@ -331,7 +333,7 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[5], long long *steps, int res
  * address; make that first call before any stream capture.  Later calls look the
  * address up again (a device reset may move it).  Systems whose workspace (as
  * rbl_workspace_size reports) exceeds 48 MiB are rejected with RBL_ENOMEM (about
- * 60,000 particles at rho* = 0.8 with the default radii); invalid parameters with
+ * 44,000 particles at rho* = 0.8 with the default radii); invalid parameters with
  * RBL_EINVAL, and so is RBL_POT_LJ_EWALD (this call takes no charges).  Every call
  * shares the array, so calls that overlap on the GPU (two streams, two host threads)
  * race: serialise them.  Each call resets the parts it reads; the array keeps the

@@ -55,6 +55,7 @@ __global__ void k_zero(View v, int conditional)
         q.nc_max = 0;
         q.ns_max = 0;
         q.m_max = 0;
+        q.t_max = 0;
         q.ns_sum = 0ull;
         q.nc_sum = 0ull;
         q.m_sum = 0ull;
@@ -268,18 +269,82 @@ __global__ void k_copy_back(View v, int conditional)
     }
 }
 
-// K3: two-level lists (or the full list).  One warp per home cell: the warp walks
-// the cell's candidate sequence 32 candidates at a time (one per lane, fetched
-// once) and tests each against every particle of the cell:
+// Prologue of the list builds: the home cell's candidate segments (warp-shared starts
+// sA, lA of piece A and sB of piece B, running counts pre[0..S]) and the cell's
+// seg_tab row.  Returns M_c, the candidate count.
+__device__ __forceinline__ int cell_segments(const View &v, const Box &b, int c, int lc, int lane, int *pre, int *sA,
+                                             int *lA, int *sB)
+{
+    const int S = b.S;
+    const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
+    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+    const int nofs0 = b.nofs[0], nofs1 = b.nofs[1];
+    // segment lengths, lane k holding segments k and k + 32 (S <= kMaxSeg < 64), then
+    // their running counts by a warp scan
+    int len2[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int sg = lane + 32 * h;
+        if (sg < S) {
+            int oz = sg / nofs1, oy = sg - oz * nofs1;
+            int czz = wrap_cell(cz + b.ofs[2][oz], n2);
+            int cyy = wrap_cell(cy + b.ofs[1][oy], n1);
+            int rowbase = b.c0 + (czz * n1 + cyy) * n0;
+            int fx = wrap_cell(cx + b.ofs[0][0], n0);
+            int last = fx + nofs0 - 1;
+            int lastA = last < n0 ? last : n0 - 1;
+            int a0 = v.start[rowbase + fx];
+            int la = v.start[rowbase + lastA + 1] - a0;
+            int b0 = v.start[rowbase];
+            int lb = last >= n0 ? v.start[rowbase + (last - n0) + 1] - b0 : 0;
+            sA[sg] = a0;
+            lA[sg] = la;
+            sB[sg] = b0;
+            len2[h] = la + lb;
+        }
+    }
+    int carry = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int x = len2[h];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        x += carry;
+        const int sg = lane + 32 * h;
+        if (sg < S) pre[sg + 1] = x;
+        carry = __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) pre[0] = 0;
+    __syncwarp();
+    const int M = pre[S];
+    int4 *gt = v.seg_tab + (size_t)c * v.S;
+    for (int sg = lane; sg < v.S; sg += 32) {
+        if (sg < S) {
+            const int split = pre[sg] + lA[sg];
+            gt[sg] = make_int4(sA[sg] - pre[sg], split, sB[sg] - split, pre[sg + 1]);
+        } else {
+            gt[sg] = make_int4(0, M, 0, M);
+        }
+    }
+    return M;
+}
+
+// K3: the lists.  One warp per home cell: the warp takes candidates 32 at a time (one
+// per lane, fetched once) and tests each against every particle of the cell:
 //   core : r2 <  (r_c + skin)^2                         -> explicit list (ballot rank)
 //   shell: max(r_c - skin, 0)^2 <= r2 < (r_s + skin)^2  -> mask word (ballot)
 //   full : r2 <  (r_s + skin)^2   (full_list mode: explicit row-major rows, no mask)
 // Candidates are visited in canonical order, so list order and bit order are the
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
-// k.  Row lengths are counted past the core capacity.  With stencil-pool sampling
-// (the paper's own pool) only the core row is built, from the 27 cells around the
-// home cell, and a particle's pool size is its home cell's stencil population less
-// itself; the segment table still spans the whole stencil, for the batch.
+// k.  Row lengths are counted past the core capacity.  k_build_lists serves the
+// stencil pool (the paper's own pool), where only the core row is built, from the 27
+// cells around the home cell, and a particle's pool size is its home cell's stencil
+// population less itself (the segment table spans the whole stencil, for the batch);
+// k_build_culled serves shell sampling and the full list, testing only the candidates
+// that survive a cull against the cell's bounding box.
 constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
 // LIST: kListShell (core row + shell mask), kListFull (full-list rows), kListPool
@@ -306,40 +371,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
     const int S = b.S;
-    const int nofs0 = b.nofs[0], nofs1 = b.nofs[1];
-    for (int sg = lane; sg < S; sg += 32) {
-        int oz = sg / nofs1, oy = sg - oz * nofs1;
-        int czz = wrap_cell(cz + b.ofs[2][oz], n2);
-        int cyy = wrap_cell(cy + b.ofs[1][oy], n1);
-        int rowbase = b.c0 + (czz * n1 + cyy) * n0;
-        int fx = wrap_cell(cx + b.ofs[0][0], n0);
-        int last = fx + nofs0 - 1;
-        int lastA = last < n0 ? last : n0 - 1;
-        int a0 = v.start[rowbase + fx];
-        int la = v.start[rowbase + lastA + 1] - a0;
-        int b0 = v.start[rowbase];
-        int lb = last >= n0 ? v.start[rowbase + (last - n0) + 1] - b0 : 0;
-        sA[sg] = a0;
-        lA[sg] = la;
-        sB[sg] = b0;
-        pre[sg + 1] = la + lb;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        pre[0] = 0;
-        for (int sg = 1; sg <= S; ++sg) pre[sg] += pre[sg - 1];
-    }
-    __syncwarp();
-    const int M = pre[S];
-    int4 *gt = v.seg_tab + (size_t)c * v.S;
-    for (int sg = lane; sg < v.S; sg += 32) {
-        if (sg < S) {
-            const int split = pre[sg] + lA[sg];
-            gt[sg] = make_int4(sA[sg] - pre[sg], split, sB[sg] - split, pre[sg + 1]);
-        } else {
-            gt[sg] = make_int4(0, M, 0, M);
-        }
-    }
+    const int M = cell_segments(v, b, c, lc, lane, pre, sA, lA, sB);
     const int s0 = v.start[c], s1 = v.start[c + 1];
     if (s1 == s0) return;
     // the masks index this cell's candidate sequence: remember the cell until the
@@ -500,6 +532,224 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     }
 }
 
+// Culled list build (shell rows with their candidate table, or full rows).  One warp
+// per home cell, as k_build_lists, with one step in front of the pair tests: each
+// candidate (one per lane, fetched once) is first tested against the bounding box of
+// the cell's particles, and only the candidates that some particle of the cell may
+// reach go on, compacted in order into a ring of kRing entries; every 32 of them form
+// one dense chunk that is tested against each particle of the pass with the
+// canonical pair rule.  Dense chunk k is mask word k (shell mode) and entries
+// 32k .. 32k + 31 of the cell's candidate table ctab, so masks index the table; the
+// rows, which only ever hold candidates within r_s + skin, are those of the full
+// candidate sequence.
+//
+// The cull is conservative.  Along axis a the box is the arc [c_a - hl_a, c_a + hh_a]
+// of the periodic fixed-point circle (2^32 units) around its centre c_a; e_a, the
+// candidate's offset from c_a as int32 (its minimum image), gives the circular gap
+// g_a = max(0, e_a - hh_a, -e_a - hl_a), and |(int32)(u_i - u_j)|_a >= g_a for every
+// particle i of the cell, in a box of any size.  The pair rule's r2 is then at least
+// (1 - 2^-21) sum_a (g_a h_a)^2 (each of its six binary32 operations rounds by at
+// most 2^-24), and the cull's own binary32 estimate of that sum (with hl, hh rounded
+// up) exceeds it by less than 2^-20, so a candidate whose estimate is at least
+// (r_s + skin)^2 (1 + 2^-12) is beyond the list cutoff for every particle.
+constexpr int kRing = 64;
+
+// Shared memory of one warp of k_build_culled (dynamic: build_warps of them per block).
+struct CullWarpSmem {
+    int4 rp[kRing];           // ring of kept candidates: images
+    int4 pos[32];             // the pass's particles
+    int rj[kRing];            // ring: particle indices
+    int pre[kMaxSeg + 1], a[kMaxSeg], la[kMaxSeg], b[kMaxSeg]; // candidate segments
+};
+
+// 64 registers (four blocks of the largest shape per SM): measured faster than the
+// unbounded 80 despite a few spilled bytes (316.7 against 353.7 us at N = 2^18).
+template <int LIST>
+__global__ void __launch_bounds__(kMaxBuildWarps * 32, 4) k_build_culled(View v, int conditional)
+{
+    if (skip(v, conditional)) return;
+    extern __shared__ int4 s_cull[];
+    constexpr bool full = LIST == kListFull;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CullWarpSmem &sm = reinterpret_cast<CullWarpSmem *>(s_cull)[warp];
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= v.ncell) return; // whole warp; no block-wide barrier below
+    const int r = v.cell_rep[c];
+    const Box &b = v.box[r];
+    const int lc = c - b.c0;
+    if (lc == b.ncell || !active(v, conditional, r)) return; // pad cell, or not rebuilding
+    const int M = cell_segments(v, b, c, lc, lane, sm.pre, sm.a, sm.la, sm.b);
+    const int S = b.S;
+    const int s0 = v.start[c], s1 = v.start[c + 1];
+    if (s1 == s0) return;
+    for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
+    RepScalars &rsc = v.rs[r];
+    const float h[3] = {b.h[0], b.h[1], b.h[2]};
+    // bounding box of the cell's particles in fixed-point units relative to its first
+    // particle (differences as int32: a cell spans less than half the box), then its
+    // centre and half-widths, rounded up as binary32
+    const int4 p0 = v.pos[s0];
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int i = s0 + lane; i < s1; i += 32) {
+        const int4 p = v.pos[i];
+        const int d[3] = {(int)((unsigned)p.x - (unsigned)p0.x), (int)((unsigned)p.y - (unsigned)p0.y),
+                          (int)((unsigned)p.z - (unsigned)p0.z)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], d[a]);
+            hi[a] = max(hi[a], d[a]);
+        }
+    }
+    unsigned cen[3];
+    float hlf[3], hhf[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        const int mid = lo[a] + ((hi[a] - lo[a]) >> 1);
+        cen[a] = (a == 0 ? (unsigned)p0.x : a == 1 ? (unsigned)p0.y : (unsigned)p0.z) + (unsigned)mid;
+        hlf[a] = __int2float_ru(mid - lo[a]);
+        hhf[a] = __int2float_ru(hi[a] - mid);
+    }
+    int *ctab_c = v.ctab + (size_t)c * v.Mcap;
+    const size_t N = (size_t)v.N;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int wmc = 0, wms = 0;
+    unsigned long long wsc = 0ull, wss = 0ull;
+    for (int base = s0; base < s1; base += 32) {
+        const int mm = min(32, s1 - base);
+        const int i_me = base + lane; // the particle this lane stores for (lane < mm)
+        if (lane < mm) sm.pos[lane] = v.pos[i_me];
+        __syncwarp();
+        int my_nc = 0, my_ns = 0;
+        int head = 0, tail = 0, kd = 0;
+        // one dense chunk: ring entries head .. head + nd - 1 against every particle
+        // of the pass (mask word kd, table entries 32 kd ..)
+        auto dense = [&](int nd) {
+            const bool dv = lane < nd;
+            const int slot = (head + lane) & (kRing - 1);
+            const int jd = sm.rj[slot];
+            const int4 pd = sm.rp[slot];
+            const bool room = full || kd < v.W; // table and masks hold W words' worth
+            if (!full && base == s0 && dv && room) ctab_c[(kd << 5) + lane] = jd;
+            unsigned my_shell = 0u, my_core = 0u;
+            for (int q = 0; q < mm; ++q) {
+                PairGeom g = pair_geom(sm.pos[q], pd, h);
+                const bool other = dv && jd != base + q;
+                if constexpr (full) {
+                    const bool in = other && g.r2 < v.t_cut_list;
+                    const unsigned bf = __ballot_sync(0xffffffffu, in);
+                    const int n0q = __shfl_sync(0xffffffffu, my_nc, q);
+                    if (in) {
+                        const int rk = n0q + __popc(bf & lt_mask);
+                        if (rk < v.cap_c) v.core[(size_t)(base + q) * (size_t)v.cap_c + rk] = jd;
+                    }
+                    if (lane == q) my_nc += __popc(bf);
+                } else {
+                    const bool in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
+                    const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
+                    my_shell = lane == q ? bs : my_shell;
+                    const bool in_core = other && g.r2 < v.t_core_list;
+                    const unsigned bc = __ballot_sync(0xffffffffu, in_core);
+                    my_core = lane == q ? bc : my_core;
+                }
+            }
+            if (lane < mm && !full && room) {
+                v.mask[(size_t)kd * N + i_me] = my_shell; // coalesced across lanes
+                my_ns += __popc(my_shell);
+                while (my_core) { // core row in candidate order
+                    const int bb = __ffs(my_core) - 1;
+                    my_core &= my_core - 1u;
+                    if (my_nc < v.cap_c) v.core[(size_t)my_nc * N + i_me] = sm.rj[(head + bb) & (kRing - 1)];
+                    ++my_nc;
+                }
+            }
+            __syncwarp();
+            head += nd;
+            ++kd;
+        };
+        // the candidates segment by segment (each a run of particle indices in one or
+        // two pieces), 32 at a time: cull, append the kept ones to the ring in order,
+        // and test every full chunk of 32 as soon as it is there
+        for (int sg = 0; sg < S; ++sg) {
+            const int a0 = sm.a[sg], la = sm.la[sg], b0 = sm.b[sg];
+            const int n_sg = sm.pre[sg + 1] - sm.pre[sg];
+            for (int o0 = 0; o0 < n_sg; o0 += 32) {
+                const int off = o0 + lane;
+                bool keep = false;
+                int j = 0;
+                int4 pj = make_int4(0, 0, 0, 0);
+                if (off < n_sg) {
+                    j = off < la ? a0 + off : b0 + (off - la);
+                    pj = v.pos[j];
+                    const int e[3] = {(int)((unsigned)pj.x - cen[0]), (int)((unsigned)pj.y - cen[1]),
+                                      (int)((unsigned)pj.z - cen[2])};
+                    float g2 = 0.f;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float ef = __int2float_rn(e[a]);
+                        const float gap = fmaxf(0.f, fmaxf(__fsub_rn(ef, hhf[a]), __fsub_rn(-ef, hlf[a])));
+                        const float ga = __fmul_rn(gap, h[a]);
+                        g2 = __fmaf_rn(ga, ga, g2);
+                    }
+                    keep = g2 < v.t_cull;
+                }
+                const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = (tail + __popc(kb & lt_mask)) & (kRing - 1);
+                    sm.rj[slot] = j;
+                    sm.rp[slot] = pj;
+                }
+                tail += __popc(kb);
+                __syncwarp();
+                if (tail - head >= 32) dense(32); // at most one: fewer than 32 were pending
+            }
+        }
+        if (tail > head) dense(tail - head);
+        if (!full && base == s0 && lane == 0) v.ctab_n[c] = tail;
+        if (!full && tail > v.Mcap) {
+            // the culled table outgrew its capacity: flag it and leave these particles
+            // with empty rows, so that no kernel decodes a mask that was not written
+            my_nc = my_ns = 0;
+            if (lane == 0) atomicOr(&v.sc->flags, kFlagCellOverflow);
+        }
+        if (lane == 0) atomicMax(&rsc.t_max, tail);
+        if (lane < mm) {
+            if (full) { // the full row's length, counted as the shell's
+                my_ns = my_nc;
+                my_nc = 0;
+                if (my_ns > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
+            }
+            v.n_core[i_me] = my_nc;
+            v.n_shell[i_me] = my_ns;
+            if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
+            wmc = max(wmc, my_nc);
+            wms = max(wms, my_ns);
+            wsc += (unsigned long long)my_nc;
+            wss += (unsigned long long)my_ns;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wmc = max(wmc, __shfl_xor_sync(0xffffffffu, wmc, o));
+        wms = max(wms, __shfl_xor_sync(0xffffffffu, wms, o));
+        wsc += __shfl_xor_sync(0xffffffffu, wsc, o);
+        wss += __shfl_xor_sync(0xffffffffu, wss, o);
+    }
+    if (lane == 0) {
+        atomicMax(&rsc.nc_max, wmc);
+        atomicMax(&rsc.ns_max, wms);
+        atomicMax(&rsc.m_max, M);
+        atomicAdd(&rsc.nc_sum, wsc);
+        atomicAdd(&rsc.ns_sum, wss);
+        atomicAdd(&rsc.m_sum, (unsigned long long)M * (unsigned long long)(s1 - s0));
+    }
+}
+
 // Graph form of the rebuild decision: set the conditional node's value from the
 // device flag the integrator raised.
 __global__ void k_set_condition(View v, cudaGraphConditionalHandle h)
@@ -545,9 +795,10 @@ cudaError_t launch_rebuild_lists(const View &v, bool conditional, cudaStream_t s
 {
     int cond = conditional ? 1 : 0;
     const dim3 gB(ceil_div(v.ncell, v.build_warps)), bB(v.build_warps * 32);
+    const size_t smem = sizeof(CullWarpSmem) * (size_t)v.build_warps;
     if (v.sampling) k_build_lists<kListPool><<<gB, bB, 0, s>>>(v, cond);
-    else if (v.full_list) k_build_lists<kListFull><<<gB, bB, 0, s>>>(v, cond);
-    else k_build_lists<kListShell><<<gB, bB, 0, s>>>(v, cond);
+    else if (v.full_list) k_build_culled<kListFull><<<gB, bB, smem, s>>>(v, cond);
+    else k_build_culled<kListShell><<<gB, bB, smem, s>>>(v, cond);
     k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
     k_finish_all<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();

@@ -141,7 +141,18 @@ Geo replica_geo(const rbl_params *p, int N)
     }
     g.ncell = (int)nc;
     g.S = g.nofs3[1] * g.nofs3[2];
-    int mcap = p->cap_stencil > 0 ? p->cap_stencil : (int)std::ceil(1.3 * rho * span + 96.0);
+    // shell sampling: the masks index a cell's culled candidate table, the stencil
+    // members within R = r_s + skin of the cell, so within the cell's box grown by R
+    // (box + slabs + quarter cylinders + ball); the stencil bounds it too
+    double vol = span;
+    if (!pool && !p->full_list) {
+        double w[3], R = p->r_s + p->skin;
+        for (int a = 0; a < 3; ++a) w[a] = p->L[a] / g.n3[a];
+        const double grown = w[0] * w[1] * w[2] + 2.0 * R * (w[0] * w[1] + w[1] * w[2] + w[2] * w[0]) +
+                             kPi * R * R * (w[0] + w[1] + w[2]) + 4.0 / 3.0 * kPi * R * R * R;
+        vol = grown < span ? grown : span;
+    }
+    int mcap = p->cap_stencil > 0 ? p->cap_stencil : (int)std::ceil(1.3 * rho * vol + 96.0);
     g.mcap = mcap > N ? N : mcap;
     g.core_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_c + p->skin, 3);
     g.full_mean = rho * 4.0 / 3.0 * kPi * std::pow(p->r_s + p->skin, 3);
@@ -197,6 +208,8 @@ Plan make_plan(const rbl_params *prm, int R, const int *Ns)
         4 * ((size_t)P.ncell + 1), 4 * ((size_t)P.ncell + 1), 4 * ((size_t)P.ncell + 1), // counts, start, fill
         4 * ((size_t)P.n_scan_blocks + 1),          // blocksums
         16 * (size_t)P.ncell * (size_t)P.S,         // seg_tab
+        P.W > 0 ? 4 * (size_t)P.ncell * (size_t)P.Mcap : 0, // ctab (shell sampling)
+        P.W > 0 ? 4 * (size_t)P.ncell : 0,          // ctab_n
         4 * Nz * (size_t)P.cap_c, 4 * Nz,           // core, n_core
         4 * Nz * (size_t)P.W, 4 * Nz,               // mask, n_shell
         4 * Nz,                                     // hcell
@@ -291,6 +304,7 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.t_core_list = (float)((rc + sk) * (rc + sk));
     v.t_shell_lo = (float)(lo * lo);
     v.t_cut_list = (float)((rs + sk) * (rs + sk));
+    v.t_cull = (float)((rs + sk) * (rs + sk) * (1.0 + 1.0 / 4096.0));
     v.t_rc2 = (float)(rc * rc);
     v.t_rs2 = (float)(rs * rs);
     v.t_disp = (float)(0.25 * sk * sk);
@@ -315,6 +329,8 @@ void assign_view(View &v, const rbl_params *prm, const Plan &P, char *base)
     v.fill = (int *)(base + P.off[k++]);
     v.blocksums = (int *)(base + P.off[k++]);
     v.seg_tab = (int4 *)(base + P.off[k++]);
+    v.ctab = (int *)(base + P.off[k++]);
+    v.ctab_n = (int *)(base + P.off[k++]);
     v.core = (int *)(base + P.off[k++]);
     v.n_core = (int *)(base + P.off[k++]);
     v.mask = (unsigned *)(base + P.off[k++]);
@@ -373,9 +389,9 @@ rbl_status check_flags(rbl_ctx *ctx, bool replicas = false)
         int nc = 0, m = 0;
         for (int r = 0; r < ctx->R; ++r) {
             nc = ctx->h_rs[r].nc_max > nc ? ctx->h_rs[r].nc_max : nc;
-            m = ctx->h_rs[r].m_max > m ? ctx->h_rs[r].m_max : m;
+            m = ctx->h_rs[r].t_max > m ? ctx->h_rs[r].t_max : m;
         }
-        set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest stencil population %d / cap %d)", nc,
+        set_err(ctx, "capacity exceeded (longest core row %d / cap %d, largest candidate table %d / cap %d)", nc,
                 ctx->view.cap_c, m, ctx->view.Mcap);
         return RBL_EOVERFLOW;
     }
@@ -1035,26 +1051,28 @@ rbl_status rbl_get_lists(rbl_ctx *ctx, int kind, int *rows, int cap, int *counts
         }
         return RBL_OK;
     }
-    // decode the masks on the host with the same segment walk as the kernels
+    // decode the masks on the host: bit b of word w is entry 32 w + b of the home
+    // cell's culled candidate table
     std::vector<unsigned> mask(N * (size_t)v.W);
-    std::vector<int4> tab((size_t)v.ncell * v.S);
+    std::vector<int> ctab(v.W > 0 ? (size_t)v.ncell * v.Mcap : 0);
     std::vector<int> hcell(N);
-    CK(cudaMemcpy(mask.data(), v.mask, mask.size() * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(tab.data(), v.seg_tab, tab.size() * 16, cudaMemcpyDeviceToHost));
+    if (v.W > 0) {
+        CK(cudaMemcpy(mask.data(), v.mask, mask.size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ctab.data(), v.ctab, ctab.size() * 4, cudaMemcpyDeviceToHost));
+    }
     CK(cudaMemcpy(hcell.data(), v.hcell, 4 * N, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < N; ++i) {
         if (row_of[i] < 0) continue;
         const size_t t = (size_t)row_of[i];
         counts[t] = cnt[i];
-        SegCursor cur;
-        cur.init(tab.data() + (size_t)hcell[i] * v.S);
+        const int *crow = ctab.data() + (size_t)hcell[i] * v.Mcap;
         int k = 0;
         for (int w = 0; w < v.W && k < cnt[i]; ++w) {
             unsigned word = mask[(size_t)w * N + i];
             while (word) {
                 int bit = __builtin_ctz(word);
                 word &= word - 1u;
-                rows[t * cap + k++] = tag[cur.index_of((w << 5) + bit)];
+                rows[t * cap + k++] = tag[crow[(w << 5) + bit]];
             }
         }
     }
@@ -1090,7 +1108,7 @@ rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, i
     }
     std::vector<unsigned> words((size_t)v.W);
     std::vector<int> entries((size_t)v.cap_c);
-    std::vector<int4> tab((size_t)v.S);
+    std::vector<int> crow((size_t)v.Mcap);
     for (int k = 0; k < m; ++k) {
         const size_t i = (size_t)slot_of[(size_t)which[k]];
         int cnt = 0;
@@ -1115,19 +1133,19 @@ rbl_status rbl_get_rows(rbl_ctx *ctx, int kind, const long long *which, int m, i
             for (int q = 0; q < nc; ++q) out[q] = tag[entries[q]];
             continue;
         }
+        if (v.W == 0) continue; // no masks (stencil pool)
+        // bit b of mask word w is entry 32 w + b of the home cell's culled table
         int hc = 0;
         CK(cudaMemcpy(&hc, v.hcell + i, 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(tab.data(), v.seg_tab + (size_t)hc * v.S, 16 * (size_t)v.S, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(crow.data(), v.ctab + (size_t)hc * v.Mcap, 4 * (size_t)v.Mcap, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy2D(words.data(), 4, v.mask + i, 4 * N, 4, (size_t)v.W, cudaMemcpyDeviceToHost));
-        SegCursor cur;
-        cur.init(tab.data());
         int q = 0;
         for (int w = 0; w < v.W && q < cnt; ++w) {
             unsigned word = words[w];
             while (word) {
                 int bit = __builtin_ctz(word);
                 word &= word - 1u;
-                out[q++] = tag[cur.index_of((w << 5) + bit)];
+                out[q++] = tag[crow[(w << 5) + bit]];
             }
         }
     }

@@ -159,12 +159,13 @@ __global__ void k_batch(View v, unsigned long long step, int *out_j, int *out_n)
         out_n[i] = nb;
         return;
     }
+    const int *ctab = v.ctab + (size_t)v.hcell[i] * v.Mcap; // the masks index the culled table
     int q = 0, seen = 0;
     for (int w = 0; q < nb; ++w) {
         const unsigned word = v.mask[(size_t)w * N + i];
         const int cnt = __popc(word);
         while (q < nb && S[q] < seen + cnt) {
-            out_j[(size_t)i * v.p + q] = cur.index_of((w << 5) + select_bit(word, S[q] - seen));
+            out_j[(size_t)i * v.p + q] = ctab[(w << 5) + select_bit(word, S[q] - seen)];
             ++q;
         }
         seen += cnt;
@@ -214,6 +215,7 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
             if (c != self) count(cur.index_of(c), false);
         return;
     }
+    const int *ctab = v.ctab + (size_t)v.hcell[i] * v.Mcap; // the masks index the culled table
     int left = v.n_shell[i];
     for (int w = 0; left > 0; ++w) {
         unsigned word = v.mask[(size_t)w * N + i];
@@ -221,7 +223,7 @@ __global__ void k_rdf(View v, float dr, int nbins, unsigned long long *hist)
         while (word) {
             int bit = __ffs(word) - 1;
             word &= word - 1u;
-            count(cur.index_of((w << 5) + bit), false);
+            count(ctab[(w << 5) + bit], false);
         }
     }
 }

@@ -252,8 +252,11 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
         const int4 pi = v.pos[i];
         const int nc = (MODE == 0 || MODE == 3 || (MODE == 2 && !v.full_list)) ? min(v.n_core[i], v.cap_c) : 0;
         const int ns = v.n_shell[i];
-        const int4 *tab = v.seg_tab + (size_t)v.hcell[i] * v.S;
-        const int nwords = min((tab[v.S - 1].w + 31) >> 5, v.W);
+        const int hc = v.hcell[i];
+        const int4 *tab = v.seg_tab + (size_t)hc * v.S;
+        // shell sampling: the masks index the home cell's culled candidate table
+        const int *ctab = v.ctab + (size_t)hc * v.Mcap;
+        const int nwords = v.W > 0 ? min((v.ctab_n[hc] + 31) >> 5, v.W) : 0;
         // stage the mask words (independent loads, in bursts) and their running
         // popcounts
         const int nws = min(nwords, kMaskStage);
@@ -293,13 +296,12 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                 if (nwords <= kMaskStage) {
                     // Each drawn rank is resolved on its own, with no branch: the word
                     // holding it by a binary search over the staged running popcounts,
-                    // the bit by select_bit, the particle by a binary search over the
-                    // segment table's running counts.  PMAX equals p (or bounds it), so
-                    // the PMAX independent chains overlap; a data-dependent walk along
-                    // the row would diverge across the warp and serialise them.  Slots
-                    // past the batch resolve a clamped rank and are not used.
-                    const int S_ = v.S;
-                    const int top = S_ <= 32 ? 16 : 32;
+                    // the bit by select_bit, the particle by one load from the culled
+                    // candidate table.  PMAX equals p (or bounds it), so the PMAX
+                    // independent chains overlap; a data-dependent walk along the row
+                    // would diverge across the warp and serialise them.  Slots past the
+                    // batch resolve a clamped rank (an entry of the table's row) and are
+                    // not used.
 #pragma unroll
                     for (int q = 0; q < PMAX; ++q) {
                         const int tq = min(S[q], max(ns - 1, 0));
@@ -311,16 +313,7 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                             w = (mid < nws && pm <= tq) ? mid : w;
                         }
                         const int cand = (w << 5) + select_bit(s_mask[w * bd + t], tq - (int)s_pref[w * bd + t]);
-                        int sg = 0;
-#pragma unroll
-                        for (int sw = 32; sw >= 1; sw >>= 1) {
-                            if (sw > top) continue;
-                            const int m2 = sg + sw;
-                            const int end = __ldg(&tab[min(m2, S_) - 1].w);
-                            sg = (m2 <= S_ && end <= cand) ? m2 : sg;
-                        }
-                        const int4 e = __ldg(&tab[min(sg, S_ - 1)]);
-                        J[q] = cand < e.y ? e.x + cand : e.z + cand;
+                        J[q] = __ldg(&ctab[cand]);
                     }
                 } else {
                     // rows longer than the staging area: walk the row in order
@@ -337,7 +330,7 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                                 word = mask_word(++w);
                                 cnt = __popc(word);
                             }
-                            J[q] = cur.index_of((w << 5) + select_bit(word, tq - seen));
+                            J[q] = ctab[(w << 5) + select_bit(word, tq - seen)];
                         }
                     }
                 }
@@ -374,7 +367,7 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                                 word = mask_word(++w);
                                 cnt = __popc(word);
                             }
-                            jj[u] = cur.index_of((w << 5) + select_bit(word, tq - seen));
+                            jj[u] = ctab[(w << 5) + select_bit(word, tq - seen)];
                         }
                     }
                     acc.template pairs<kGather>(v, pi, i, jj, nb - q0, 1);
@@ -496,7 +489,7 @@ __global__ void __maxnreg__((FP32 ? ForceTuning<MODE, ENERGY, EWALD>::regs : 128
                         while (word == 0u) word = mask_word(++w);
                         const int bit = __ffs(word) - 1;
                         word &= word - 1u;
-                        jj[u] = cur.index_of((w << 5) + bit);
+                        jj[u] = ctab[(w << 5) + bit];
                     }
                 }
                 acc.template pairs<kGather>(v, pi, i, jj, ns - k0, 1);

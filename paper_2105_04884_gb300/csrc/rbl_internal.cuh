@@ -57,6 +57,7 @@ struct RepScalars {
     int rebuild;                    // 1 when this replica's lists must be rebuilt
     int nc_max, ns_max;             // longest rows at the last build (even past capacity)
     int m_max;                      // largest stencil population at the last build
+    int t_max;                      // longest culled candidate table at the last build (shell sampling)
     unsigned long long ns_sum;      // total shell (or full) entries at the last build
     unsigned long long nc_sum;      // total core entries at the last build
     unsigned long long m_sum;       // sum over particles of their home cell's stencil population
@@ -97,12 +98,18 @@ struct Box {
 // k < .y ? .x + k : .z + k, and .w is the running count through the segment.  Rows
 // are S = max_r S_r entries long; entries past the replica's S_r are (0, M_c, 0, M_c),
 // so seg_tab[c][S-1].w = M_c for every cell.
+// Shell sampling keeps, per home cell, the culled candidate table ctab[c][0..T_c):
+// the candidate sequence without the candidates that no particle of the cell can
+// reach (farther than r_s + skin, with a margin that covers every binary32 rounding
+// of the pair rule, from the bounding box of the cell's particles at the build), in
+// the same order.  A dropped candidate is in no row of the cell, so rows are the
+// same whichever sequence the masks index.
 // Per particle slot:
 //   core  : explicit list of neighbour indices, column-major core[k][N];
-//   shell : bitmask over the candidate sequence, column-major mask[w][N], bit b of
-//           word w <-> candidate 32 w + b (full list in full_list mode).
-// A shell row in canonical order is the candidate sequence filtered by the mask, so
-// the position of a neighbour in its row is its rank among the set bits.
+//   shell : bitmask over the culled table, column-major mask[w][N], bit b of word w
+//           <-> ctab entry 32 w + b (full_list mode: explicit rows in core instead).
+// A shell row in canonical order is the table filtered by the mask, so the position
+// of a neighbour in its row is its rank among the set bits.
 struct View {
     int N;                          // particle slots of all replicas (stride of per-particle arrays)
     int R;                          // replicas
@@ -116,6 +123,7 @@ struct View {
     int build_warps;                // home cells (warps) per block of the list build (2, 4 or 8)
     int ncell;                      // cells of all replicas, pad cells included
     float t_core_list, t_shell_lo, t_cut_list, t_rc2, t_rs2, t_disp;
+    float t_cull;                   // (r_s + skin)^2 (1 + 2^-12): the list build's bounding-box cull
     double dt, gamma, c1;
     const Box *box;                 // [R]
     const int2 *tile;               // [ntile]: (replica, end of its live slots)
@@ -133,6 +141,9 @@ struct View {
     int *cell, *order;
     int *counts, *start, *fill, *blocksums;
     int4 *seg_tab;                  // [ncell][S]
+    int *ctab;                      // [ncell][Mcap]: culled candidate table (shell sampling; Mcap
+                                    // is its capacity, W = Mcap / 32 mask words)
+    int *ctab_n;                    // [ncell]: its length T_c
     int *core, *n_core;             // core[k * N + i], k < cap_c
     unsigned *mask;                 // mask[w * N + i], w < W
     int *n_shell;                   // set bits in the mask (N_s, or full-list length)

@@ -1,11 +1,11 @@
 """Failure detection through the C ABI, with no GPU fault: the kernels record a
 problem in the context's device flags and keep every access inside the arrays (rows
-are written only up to their capacity; a cell whose stencil exceeds the mask
-capacity gets empty rows), and the next synchronising call turns the flag into a
+are written only up to their capacity; a cell whose culled candidate table exceeds
+its capacity gets empty rows), and the next synchronising call turns the flag into a
 status.
 
 - a core row longer than its capacity -> RBL_EOVERFLOW (rows truncated, counts kept);
-- a stencil population beyond the mask capacity -> RBL_EOVERFLOW;
+- a culled candidate table beyond its capacity (cap_stencil) -> RBL_EOVERFLOW;
 - non-finite input positions -> RBL_ENONFINITE at rbl_set_state;
 - finite input that turns bad during a step (two particles 0.05 sigma apart, or at
   the same place): the binary32 force leaves the fixed-point range or is NaN (FP32
@@ -47,7 +47,7 @@ def test_core_row_overflow(fluid):
 
 def test_stencil_overflow(fluid):
     x, v, L = fluid
-    s = rbl.System(x, v, L, cap_stencil=64, **ARGS)  # ~740 candidates per home cell
+    s = rbl.System(x, v, L, cap_stencil=64, **ARGS)  # ~350 culled candidates per home cell
     with pytest.raises(rbl.RblError) as e:
         s.step(2)
     assert e.value.status == 3
