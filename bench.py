@@ -709,21 +709,19 @@ def run_ours(a, rank, world, local):
     nc, ns, p = obs["Nc_mean"], obs["Ns_mean"], w["p"]
     # Roofline of the RBL force kernel (K4).  Algorithmic bytes per particle, the data
     # the method must move: own position 16, core row 4 n_c, N_s 4, the p sampled shell
-    # entries 4 p, force out 24.  The bytes of this build's layout (row counts and home
-    # cell 12, core row, every shell mask word of the home cell's stencil 4 ceil(M_c/32),
-    # the cell's share of the segment table 16 S ncell / N, force 24) and the DRAM
-    # traffic ncu measured are reported beside it.
-    S = 25 if w["K"] == 2 else (2 * w["K"] + 1) ** 2
-    ncell = int(math.floor(L[0] * w["K"] / (w["rs"] + w["skin"]))) ** 3
+    # entries 4 p, force out 24.  The DRAM traffic ncu measured for this build's layout
+    # (row counts and home cell, core row, the shell mask words over the home cell's
+    # culled table, one 32-byte sector of that table per drawn entry, force) is reported
+    # beside it, with the fraction it gives.
     alg_force = 16 + 4 * nc + 4 + 4 * p + 24 + qself
-    layout_force = 16 + 12 + 4 * nc + 4 * math.ceil(obs["Mc_mean"] / 32) + 16 * S * ncell / N + 24 + qself
     t_force = ph["force_kernel"] * 1e-3
     traffic_f = load_traffic(N, "force_kernel_traffic_ewald.json" if ewald else "force_kernel_traffic.json")
     roof_force = {"kernel": kname, "bound": "hbm", "achieved": alg_force * N / t_force / 1e9, "peak": peak,
                   "unit": "GB/s", "frac": alg_force * N / t_force / 1e9 / peak, "peak_source": peak_kind,
-                  "algorithmic_bytes_per_particle": alg_force, "layout_bytes_per_particle": layout_force,
-                  "layout_frac": layout_force * N / t_force / 1e9 / peak,
+                  "algorithmic_bytes_per_particle": alg_force,
                   "traffic": traffic_f, "traffic_per": "launch", "ms_per_launch": ph["force_kernel"]}
+    if traffic_f is not None:
+        roof_force["traffic_frac"] = traffic_f / t_force / 1e9 / peak
     # Roofline of the list build (K3), per rebuild: own position 16 and the rows, core
     # and shell, as 4-byte entries 4 (n_c + N_s) (the same bytes as the survey's
     # estimate of ~800 B per particle per rebuild).  Its launches inside the phase-timed
@@ -732,7 +730,8 @@ def run_ours(a, rank, world, local):
     alg_build = 16 + 4 * (nc + ns)
     t_build = ph["list_build"] * nsteps / max(rebuilds_phase, 1) * 1e-3
     traffic_b = load_traffic(N, "list_build_traffic.json")
-    roof_build = {"kernel": "k_build_lists<0> (core row + shell mask, one warp per home cell)", "bound": "hbm",
+    roof_build = {"kernel": "k_build_culled<0> (bounding-box cull into the cell's candidate table, then core row + "
+                            "shell mask; one warp per home cell)", "bound": "hbm",
                   "achieved": alg_build * N / t_build / 1e9, "peak": peak, "unit": "GB/s",
                   "frac": alg_build * N / t_build / 1e9 / peak, "peak_source": peak_kind,
                   "algorithmic_bytes_per_particle": alg_build, "traffic": traffic_b, "traffic_per": "launch",
@@ -752,16 +751,15 @@ def run_ours(a, rank, world, local):
                    "timed_path": "rbl_step(K): CUDA graph replays, one per step (the rebuild chain behind a "
                                  "device-side IF node)"},
         # per step: integrate, the rebuild condition, force kernel and its reduction;
-        # the 12 rebuild-chain kernels on the steps that rebuild; on the last step the
-        # energy sums' chunk reduction and the closing half-kick
-        "gpu_launches": 4 * a.steps + 12 * rebuilds + 2,
+        # the 12 rebuild-chain kernels on the steps that rebuild
+        "gpu_launches": 4 * a.steps + 12 * rebuilds,
         "phases_ms_per_step": ph,
         "phase_timed_ms_per_step": ms_phase / a.steps,
         "rebuilds_in_timed_region": rebuilds,
         "rows": {"core_mean": nc, "shell_mean": ns, "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"],
                  "stencil_mean": obs["Mc_mean"]},
         "roofline": dominant,
-        "rooflines": {"k_build_lists": roof_build, "k_force": roof_force},
+        "rooflines": {"k_build_culled": roof_build, "k_force": roof_force},
         "clocks": clk,
         "launch_config": tuned,
     }

@@ -256,7 +256,8 @@ __device__ __forceinline__ T wsum(T x)
 }
 
 // Observables launch, part 1: the kinetic sums of one tile (256 slots) per warp.
-// Each lane sums its 8 slots in order; the four per-lane sums (v^2, v_x, v_y, v_z) are
+// Each lane sums its 8 slots in order (v^2 per axis, then the three added); the four
+// per-lane sums (v^2, v_x, v_y, v_z) are
 // then reduced over the warp by one fixed transposed shuffle tree (6 FP64 additions
 // per lane instead of 20: the first level halves the values a lane carries, the
 // second halves them again), after which lanes 8k hold the tile's sum of value k.
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(View v, double ck, do
         const size_t base = (size_t)tile * kTile + lane;
         const int2 tl = v.tile[tile];
         const RepScalars *rsc = v.rs + tl.x;
-        double x[4] = {0, 0, 0, 0};
+        // per axis, so that no chain of dependent FP64 operations is longer than 8
+        double q2[3] = {0, 0, 0}, x[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int k = 0; k < kTile / 32; ++k) {
             const size_t i = base + (size_t)k * 32;
@@ -294,10 +296,11 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(View v, double ck, do
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double va = live ? kick_v<FP32>(v, rsc, (int)i, tag, a, ck, cks) : 0.0;
-                x[0] = fma(va, va, x[0]);
+                q2[a] = fma(va, va, q2[a]);
                 x[1 + a] += va;
             }
         }
+        x[0] = (q2[0] + q2[1]) + q2[2];
         // level 16: lanes below 16 keep values 0, 1, the others 2, 3
         const bool u16 = (lane & 16) != 0;
         double a0 = u16 ? x[2] : x[0], a1 = u16 ? x[3] : x[1];
