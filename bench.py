@@ -134,7 +134,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -696,13 +696,23 @@ def run_ours(a, rank, world, local):
     obs0 = s.observables()
     ms_phase, (phase_ms, nsteps) = timed(s, a.steps, phases=True)
     obs1 = s.observables()
+    # clocks: sampled every 20 ms from just before the timed region through a 1000-step
+    # steady-state run of the same workload right after it (the timed region alone is
+    # ~10 ms); the steady-state run is reported beside the K-step value (a K-step window
+    # holds whichever rebuilds fall in it)
     clocks = Clocks(local)
     clocks.start()
+    obs_pre = s.observables()  # rebuild count at the start of the timed steps
     ms, _ = timed(s, a.steps, phases=False)
+    obs_post = s.observables()
+    LONG = 1000
+    ms_long, _ = timed(s, LONG, phases=False)
     clk = clocks.stop()
-    obs = s.observables()
+    clk["window"] = "the %d timed steps and the %d-step steady-state run right after them" % (a.steps, LONG)
+    obs_long = s.observables()
+    obs = obs_post
     value = whole_job_rate(N, a.steps, world, ms)
-    rebuilds = obs["n_rebuild"] - obs1["n_rebuild"]
+    rebuilds = obs["n_rebuild"] - obs_pre["n_rebuild"]
     rebuilds_phase = obs1["n_rebuild"] - obs0["n_rebuild"]
     ph = phase_dict(phase_ms, nsteps)
     peak, peak_kind = load_peaks()
@@ -756,6 +766,10 @@ def run_ours(a, rank, world, local):
         "phases_ms_per_step": ph,
         "phase_timed_ms_per_step": ms_phase / a.steps,
         "rebuilds_in_timed_region": rebuilds,
+        "steady_state": {"steps": LONG, "ms_per_step": ms_long / LONG,
+                         "value": whole_job_rate(N, LONG, world, ms_long),
+                         "rebuilds": obs_long["n_rebuild"] - obs_post["n_rebuild"],
+                         "path": "the same rbl_step graph path, timed right after the K timed steps"},
         "rows": {"core_mean": nc, "shell_mean": ns, "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"],
                  "stencil_mean": obs["Mc_mean"]},
         "roofline": dominant,

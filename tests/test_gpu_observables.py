@@ -86,3 +86,36 @@ def test_step_async_equals_step():
     assert sa == sb == 30
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert b.read_obs(buf)[0] == a.observables()
+
+
+def test_state_through_page_locked_buffers():
+    """rbl_set_state / rbl_get_state with page-locked host buffers (read and written by
+    the kernels themselves, no staging copy) give exactly what pageable host buffers and
+    device buffers give, for an ensemble with a pending half kick."""
+    import ctypes
+
+    reps = []
+    for r, (N, rho, T) in enumerate([(700, 0.8, 1.2), (1500, 0.7, 1.8)]):
+        x, L = inputs.fcc(N, rho, 0.05, seed=60 + r)
+        reps.append(rbl.Replica(x, inputs.maxwell_boltzmann(N, T, seed=60 + r), L, T, 60 + r))
+    ens = rbl.Ensemble(reps, r_c=RC, r_s=RS, skin=SKIN, p=P, dt=DT, gamma=1.0)
+    ens.step(7)  # leaves a half kick pending
+    x0, v0, step0 = ens.get_state()  # pageable host buffers
+    xd, vd, _ = ens.get_state(device=True)
+    assert np.array_equal(xd.cpu().numpy(), x0) and np.array_equal(vd.cpu().numpy(), v0)
+    xp = torch.empty(x0.shape, dtype=torch.float64).pin_memory()
+    vp = torch.empty_like(xp).pin_memory()
+    st = ctypes.c_longlong()
+    ens._check(ens.lib.rbl_get_state(ens.h, ctypes.c_void_p(xp.data_ptr()), ctypes.c_void_p(vp.data_ptr()),
+                                     ctypes.byref(st), 0))
+    assert st.value == step0
+    assert np.array_equal(xp.numpy(), x0) and np.array_equal(vp.numpy(), v0)
+    # the same state loaded from page-locked and from pageable buffers steps identically
+    ens._check(ens.lib.rbl_set_state(ens.h, ctypes.c_void_p(xp.data_ptr()), ctypes.c_void_p(vp.data_ptr()),
+                                     step0, 0))
+    ens.step(5)
+    xa, va, _ = ens.get_state()
+    ens.set_state(x0, v0, step0)
+    ens.step(5)
+    xb, vb, _ = ens.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
