@@ -339,7 +339,7 @@ __device__ __forceinline__ int cell_segments(const View &v, const Box &b, int c,
 //   full : r2 <  (r_s + skin)^2   (full_list mode: explicit row-major rows, no mask)
 // Candidates are visited in canonical order, so list order and bit order are the
 // canonical row order.  Particle k of a pass of up to 32 keeps its counters in lane
-// k.  Row lengths are counted past the core capacity.  k_build_lists serves the
+// k.  Row lengths are counted past the core capacity.  k_build_pool serves the
 // stencil pool (the paper's own pool), where only the core row is built, from the 27
 // cells around the home cell, and a particle's pool size is its home cell's stencil
 // population less itself (the segment table spans the whole stencil, for the batch);
@@ -347,13 +347,11 @@ __device__ __forceinline__ int cell_segments(const View &v, const Box &b, int c,
 // that survive a cull against the cell's bounding box.
 constexpr int kMaxBuildWarps = 8; // home cells (warps) per block: a launch parameter, 2, 4 or 8
 
-// LIST: kListShell (core row + shell mask), kListFull (full-list rows), kListPool
-// (core row only; stencil-pool sampling), fixed at compile time so that the pair-test
-// loop carries no mode branches.
-enum { kListShell = 0, kListFull = 1, kListPool = 2 };
+// LIST (k_build_culled): kListShell (core row + shell mask) or kListFull (full-list
+// rows), fixed at compile time so that the pair-test loop carries no mode branches.
+enum { kListShell = 0, kListFull = 1 };
 
-template <int LIST>
-__global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int conditional)
+__global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_pool(View v, int conditional)
 {
     if (skip(v, conditional)) return;
     __shared__ int s_pre[kMaxBuildWarps][kMaxSeg + 1];
@@ -378,27 +376,12 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     // next build, however far the particle drifts meanwhile
     for (int i = s0 + lane; i < s1; i += 32) v.hcell[i] = c;
     RepScalars &rsc = v.rs[r];
-    constexpr bool pool = LIST == kListPool; // no masks: the stencil population is not bounded by them
-    constexpr bool full = LIST == kListFull; // no masks either: explicit rows
-    if (!pool && !full && M > v.Mcap) {
-        // too many candidates for the masks: flag it and leave these particles with
-        // empty rows so that no kernel decodes a mask that was not written
-        for (int i = s0 + lane; i < s1; i += 32) {
-            v.n_core[i] = 0;
-            v.n_shell[i] = 0;
-        }
-        if (lane == 0) {
-            atomicOr(&v.sc->flags, kFlagCellOverflow);
-            atomicMax(&rsc.m_max, M);
-        }
-        return;
-    }
     const float h[3] = {b.h[0], b.h[1], b.h[2]};
     // Stencil-pool sampling: no shell rows; the core row comes from the cells within
     // one cell of the home cell (the cell edge is at least r_c + skin), taken in the
     // order they have in the full stencil, one single-cell segment each.
     int Sseg = S, Mloop = M;
-    if (pool) {
+    {
         // near offsets per axis in the stencil's order: -1, 0, 1 (offsets relative to
         // the home cell), or 0, 1, n-1 (every cell once from the home cell; fewer
         // when n < 3); lane k takes near cell k, in z-major order, then one warp scan
@@ -435,7 +418,6 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
     }
     const int nchunk = (Mloop + 31) >> 5;
     const size_t N = (size_t)v.N;
-    const unsigned lt_mask = (1u << lane) - 1u;
     int wmc = 0, wms = 0;
     unsigned long long wsc = 0ull, wss = 0ull;
     for (int base = s0; base < s1; base += 32) {
@@ -456,39 +438,17 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             seg = __shfl_sync(0xffffffffu, sg, 31);
             s_j[warp][lane] = j;
             // test the 32 candidates against each particle of the pass; lane q keeps
-            // particle q's shell and core words
-            unsigned my_shell = 0u, my_core = 0u;
+            // particle q's core word
+            unsigned my_core = 0u;
             for (int q = 0; q < mm; ++q) {
                 PairGeom g = pair_geom(s_pos[warp][q], pj, h);
                 const bool other = valid && j != base + q;
-                if constexpr (full) {
-                    // the full row of particle base + q, in candidate order: each member
-                    // lane writes its entry at the particle's count plus its rank in the
-                    // ballot (consecutive addresses of the row)
-                    const bool in = other && g.r2 < v.t_cut_list;
-                    const unsigned bf = __ballot_sync(0xffffffffu, in);
-                    const int n0q = __shfl_sync(0xffffffffu, my_nc, q);
-                    if (in) {
-                        const int rk = n0q + __popc(bf & lt_mask);
-                        if (rk < v.cap_c) v.core[(size_t)(base + q) * (size_t)v.cap_c + rk] = j;
-                    }
-                    if (lane == q) my_nc += __popc(bf);
-                }
-                if constexpr (!pool && !full) {
-                    const bool in_shell = other && g.r2 >= v.t_shell_lo && g.r2 < v.t_cut_list;
-                    const unsigned bs = __ballot_sync(0xffffffffu, in_shell);
-                    my_shell = lane == q ? bs : my_shell;
-                }
-                if constexpr (!full) {
-                    const bool in_core = other && g.r2 < v.t_core_list;
-                    const unsigned bc = __ballot_sync(0xffffffffu, in_core);
-                    my_core = lane == q ? bc : my_core;
-                }
+                const bool in_core = other && g.r2 < v.t_core_list;
+                const unsigned bc = __ballot_sync(0xffffffffu, in_core);
+                my_core = lane == q ? bc : my_core;
             }
             __syncwarp();
-            if (lane < mm && !full) {
-                if (!pool) v.mask[(size_t)k * N + i_me] = my_shell; // coalesced across lanes
-                my_ns += __popc(my_shell);
+            if (lane < mm) {
                 while (my_core) { // core row in candidate order
                     const int b = __ffs(my_core) - 1;
                     my_core &= my_core - 1u;
@@ -499,12 +459,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
             __syncwarp();
         }
         if (lane < mm) {
-            if (pool) my_ns = M - 1; // the pool: every other particle of the stencil
-            if (full) { // the full row's length, counted as the shell's
-                my_ns = my_nc;
-                my_nc = 0;
-                if (my_ns > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
-            }
+            my_ns = M - 1; // the pool: every other particle of the stencil
             v.n_core[i_me] = my_nc;
             v.n_shell[i_me] = my_ns;
             if (my_nc > v.cap_c) atomicOr(&v.sc->flags, kFlagOverflow);
@@ -533,7 +488,7 @@ __global__ void __launch_bounds__(kMaxBuildWarps * 32) k_build_lists(View v, int
 }
 
 // Culled list build (shell rows with their candidate table, or full rows).  One warp
-// per home cell, as k_build_lists, with one step in front of the pair tests: each
+// per home cell, as k_build_pool, with one step in front of the pair tests: each
 // candidate (one per lane, fetched once) is first tested against the bounding box of
 // the cell's particles, and only the candidates that some particle of the cell may
 // reach go on, compacted in order into a ring of kRing entries; every 32 of them form
@@ -796,7 +751,7 @@ cudaError_t launch_rebuild_lists(const View &v, bool conditional, cudaStream_t s
     int cond = conditional ? 1 : 0;
     const dim3 gB(ceil_div(v.ncell, v.build_warps)), bB(v.build_warps * 32);
     const size_t smem = sizeof(CullWarpSmem) * (size_t)v.build_warps;
-    if (v.sampling) k_build_lists<kListPool><<<gB, bB, 0, s>>>(v, cond);
+    if (v.sampling) k_build_pool<<<gB, bB, 0, s>>>(v, cond);
     else if (v.full_list) k_build_culled<kListFull><<<gB, bB, smem, s>>>(v, cond);
     else k_build_culled<kListShell><<<gB, bB, smem, s>>>(v, cond);
     k_finish<<<ceil_div(v.R, kBlock), kBlock, 0, s>>>(v, cond);
