@@ -719,7 +719,7 @@ def run_ours(a, rank, world, local):
     nc, ns, p = obs["Nc_mean"], obs["Ns_mean"], w["p"]
     # Roofline of the RBL force kernel (K4).  Algorithmic bytes per particle, the data
     # the method must move: own position 16, core row 4 n_c, N_s 4, the p sampled shell
-    # entries 4 p, force out 24.  The DRAM traffic ncu measured for this build's layout
+    # entries 4 p, force out 24.  The DRAM traffic ncu measured for this data layout
     # (row counts and home cell, core row, the shell mask words over the home cell's
     # culled table, one 32-byte sector of that table per drawn entry, force) is reported
     # beside it, with the fraction it gives.
@@ -733,10 +733,10 @@ def run_ours(a, rank, world, local):
     if traffic_f is not None:
         roof_force["traffic_frac"] = traffic_f / t_force / 1e9 / peak
     # Roofline of the list build (K3), per rebuild: own position 16 and the rows, core
-    # and shell, as 4-byte entries 4 (n_c + N_s) (the same bytes as the survey's
-    # estimate of ~800 B per particle per rebuild).  Its launches inside the phase-timed
-    # steps that did not rebuild return at once; the phase total is divided by the
-    # rebuilds (a slight overestimate of the per-rebuild time).
+    # and shell, as 4-byte entries 4 (n_c + N_s) (~800 B per particle per rebuild).
+    # Its launches inside the phase-timed steps that did not rebuild return at once;
+    # the phase total is divided by the rebuilds (a slight overestimate of the
+    # per-rebuild time).
     alg_build = 16 + 4 * (nc + ns)
     t_build = ph["list_build"] * nsteps / max(rebuilds_phase, 1) * 1e-3
     traffic_b = load_traffic(N, "list_build_traffic.json")
