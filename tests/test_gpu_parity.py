@@ -38,11 +38,18 @@ CASES = {
     "n2000_p1": dict(N=2000, rho=0.8, jitter=0.3, rc=1.5, rs=3.5, skin=0.3, p=1, K=2, seed=6),
     # the paper's Table 1 system: dilute, r_s = 6, r_c = 2, p = 100 (general batch path)
     "n2000_rho0.2_rs6_p100": dict(N=2000, rho=0.2, jitter=0.3, rc=2.0, rs=6.0, skin=0.3, p=100, K=2, seed=7),
+    # non-cubic boxes: a different fixed-point unit per axis in the pair rule and the
+    # list build's bounding-box cull; 5 cells along x (fewer than 2K + 3), and at K = 3
+    # 6 (fewer than 2K + 1: the stencil takes every x cell once)
+    "n2000_aniso": dict(N=2000, rho=0.8, jitter=0.15, rc=1.5, rs=3.5, skin=0.3, p=10, K=2, seed=8,
+                        L=(10.0, 12.5, 20.0)),
+    "n1500_aniso_K3": dict(N=1500, rho=0.8, jitter=0.15, rc=1.5, rs=3.5, skin=0.3, p=10, K=3, seed=9,
+                           L=(8.2, 11.0, 20.8)),
 }
 
 
 def _state(c):
-    x, L = inputs.fcc(c["N"], c["rho"], c["jitter"], seed=c["seed"])
+    x, L = inputs.fcc(c["N"], c["rho"], c["jitter"], seed=c["seed"], L=c.get("L"))
     v = inputs.maxwell_boltzmann(c["N"], 1.5, seed=c["seed"])
     return x, v, L
 
