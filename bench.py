@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-full-list", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune-cells", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-physics", action="store_true", help="skip the matched-physics block")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble block")
@@ -777,6 +778,9 @@ def run_ours(a, rank, world, local):
         "clocks": clk,
         "launch_config": tuned,
     }
+    x_tune, v_tune = None, None
+    if not a.no_tune_cells and not ewald:  # (the tuner's contexts carry no charges)
+        x_tune, v_tune, _ = s.get_state()  # the equilibrated state, for the cell-size tuner below
     # full Verlet list on the same GPU and workload
     if not a.no_full_list:
         del s
@@ -888,6 +892,17 @@ def run_ours(a, rank, world, local):
                               "unit": "particle-steps/s",
                               "path": "as e2e with rbl_step(1) and rbl_observables, each of which waits"}
         del se
+    if x_tune is not None:
+        # cells_per_cutoff by measurement (rbl_tune_cells): K decides which batches are
+        # drawn, so it is a choice made before a run; the workload's K = 2 is its result
+        torch.cuda.empty_cache()
+        kw = {k: v for k, v in common.items() if k not in ("cells_per_cutoff", "r_c", "r_s", "skin", "p", "dt")}
+        K_best, ms_k = rbl.tune_cells(x_tune, v_tune, L, common["r_c"], common["r_s"], common["skin"], common["p"],
+                                      common["dt"], steps=20, **kw)
+        result["cell_size_tuning"] = {"K_best": K_best, "ms_per_step_K1_K2_K3": ms_k,
+                                      "workload_K": w["K"], "steps": 20,
+                                      "path": "rbl_tune_cells on the equilibrated state, each K in its own context"}
+        del x_tune, v_tune
     if not a.no_ewald and not ewald:
         result["ewald"] = ewald_bench(a, world, x, v, L, common, timed)
     if not a.no_ensemble:

@@ -307,6 +307,25 @@ rbl_status rbl_density_profile(rbl_ctx *ctx, int axis, int nbins, long long *his
 rbl_status rbl_set_launch_config(rbl_ctx *ctx, int force_threads, int build_warps);
 rbl_status rbl_autotune(rbl_ctx *ctx, int trials, int *force_threads, int *build_warps);
 
+/* Cell size by measurement (the linked cells of Sec. 2 / Fig. 1: cells of width
+ * >= (r_s + skin)/K, stencil (2K + 1)^3).  K is not a launch shape: the canonical row
+ * order follows the cell stencil, so K decides which batch each step draws (every K
+ * samples the same shell rows uniformly; the oracle reproduces each K's batches), and
+ * it is chosen before a run.  rbl_tune_cells runs the caller's system (positions x,
+ * velocities v, [N][3] tag-order host arrays, read only) for K = 1, 2 and 3 in turn,
+ * each in a context of its own created in `workspace` (device memory of at least
+ * rbl_tune_cells_workspace_size bytes, the largest of the three workspaces; the call
+ * allocates nothing) with its launch shapes autotuned: `steps` warm-up steps, then
+ * `steps` steps timed with CUDA events on `stream` (use steps >= 10 so that the
+ * timing includes list rebuilds).  It returns the fastest K in *K_best and, when
+ * ms_per_step is not NULL, the three times in ms_per_step[3] (-1 for a K that the
+ * parameters do not allow or that does not fit the workspace).  prm's own
+ * cells_per_cutoff is ignored.  Errors of the trial runs are returned as they occur
+ * (a blow-up of the given state, RBL_ENONFINITE, for instance).  Synchronises. */
+rbl_status rbl_tune_cells_workspace_size(const rbl_params *prm, int N, size_t *bytes);
+rbl_status rbl_tune_cells(const rbl_params *prm, int N, const double *x, const double *v, void *workspace,
+                          size_t workspace_bytes, void *stream, int steps, int *K_best, float *ms_per_step);
+
 /* Phase timing.  While enabled, rbl_step launches each step's phases directly (no
  * graph replay) and brackets them with CUDA events on the context's stream:
  * phase 0 = kick/drift/thermostat kernel, 1 = cell hash, scan, sort and permutation,

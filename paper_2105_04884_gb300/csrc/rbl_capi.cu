@@ -1335,6 +1335,77 @@ rbl_status rbl_autotune(rbl_ctx *ctx, int trials, int *force_threads, int *build
     return check_flags(ctx);
 }
 
+// Cell size by measurement.  K sets the cell stencil, hence the canonical row order and
+// which batch each step draws, so it is chosen before a run from timings of the
+// caller's own system, each K in a context of its own (launch shapes tuned for it).
+rbl_status rbl_tune_cells_workspace_size(const rbl_params *prm, int N, size_t *bytes)
+{
+    if (!prm || !bytes) return RBL_EINVAL;
+    size_t best = 0;
+    for (int K = 1; K <= 3; ++K) {
+        rbl_params q = *prm;
+        q.cells_per_cutoff = K;
+        size_t b = 0;
+        if (rbl_workspace_size(&q, N, &b) == RBL_OK && b > best) best = b;
+    }
+    if (best == 0) return RBL_EINVAL;
+    *bytes = best;
+    return RBL_OK;
+}
+
+rbl_status rbl_tune_cells(const rbl_params *prm, int N, const double *x, const double *v, void *workspace,
+                          size_t workspace_bytes, void *stream, int steps, int *K_best, float *ms_per_step)
+{
+    if (!prm || !x || !workspace || !K_best || steps < 1) return RBL_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return RBL_ECUDA;
+    }
+    rbl_status st = RBL_OK;
+    float best = 0.f;
+    int pick = 0;
+    for (int K = 1; K <= 3 && st == RBL_OK; ++K) {
+        float ms = -1.f; // not valid for these parameters, or larger than the workspace
+        rbl_params q = *prm;
+        q.cells_per_cutoff = K;
+        size_t need = 0;
+        if (rbl_workspace_size(&q, N, &need) == RBL_OK && need <= workspace_bytes) {
+            rbl_ctx *ctx = nullptr;
+            st = rbl_create(&q, N, workspace, workspace_bytes, stream, &ctx);
+            if (st == RBL_OK) st = rbl_set_state(ctx, x, v, 0, 0);
+            if (st == RBL_OK) st = rbl_autotune(ctx, 2, nullptr, nullptr);
+            if (st == RBL_OK) st = rbl_step(ctx, steps); // warm-up, rebuilds included
+            if (st == RBL_OK) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) st = RBL_ECUDA;
+                if (st == RBL_OK) st = rbl_step_async(ctx, steps);
+                if (st == RBL_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                    st = RBL_ECUDA;
+                float t = 0.f;
+                if (st == RBL_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = RBL_ECUDA;
+                rbl_obs o;
+                if (st == RBL_OK) st = rbl_observables(ctx, &o); // waits; reports the timed steps' device flags
+                ms = t / (float)steps;
+            }
+            if (ctx) rbl_destroy(ctx);
+            if (st == RBL_OK && (pick == 0 || ms < best)) {
+                best = ms;
+                pick = K;
+            }
+        }
+        if (ms_per_step) ms_per_step[K - 1] = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (st != RBL_OK) return st;
+    if (pick == 0) return RBL_EINVAL;
+    *K_best = pick;
+    return RBL_OK;
+}
+
 rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable)
 {
     if (!ctx) return RBL_EINVAL;

@@ -65,7 +65,8 @@ EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch
            "rbl_observables_async", "rbl_exact_energy", "rbl_get_lists", "rbl_get_rows", "rbl_get_batch",
            "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config", "rbl_autotune", "rbl_set_phase_timing",
            "rbl_phase_times", "rbl_forces_static", "rbl_checkpoint_size", "rbl_save_checkpoint",
-           "rbl_load_checkpoint", "rbl_destroy", "rbl_last_error", "rbl_status_string"]
+           "rbl_load_checkpoint", "rbl_destroy", "rbl_last_error", "rbl_status_string",
+           "rbl_tune_cells_workspace_size", "rbl_tune_cells"]
 
 _lib = None
 
@@ -120,6 +121,9 @@ def load(build_if_missing: bool = False):
     L.rbl_destroy.restype = None
     L.rbl_last_error.argtypes = [P]
     L.rbl_last_error.restype = ctypes.c_char_p
+    L.rbl_tune_cells_workspace_size.argtypes = [ctypes.POINTER(rbl_params), I, ctypes.POINTER(ctypes.c_size_t)]
+    L.rbl_tune_cells.argtypes = [ctypes.POINTER(rbl_params), I, P, P, P, ctypes.c_size_t, P, I,
+                                 ctypes.POINTER(ctypes.c_int), P]
     L.rbl_status_string.argtypes = [I]
     L.rbl_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -149,6 +153,36 @@ def make_params(L, r_c, r_s, skin, p, dt, T=1.0, gamma=0.0, seed=1, precision=RB
     prm.potential = int(potential)
     prm.alpha = float(alpha)
     return prm
+
+
+def tune_cells(x, v, L, r_c, r_s, skin, p, dt, steps=20, stream=None, device=None, **kw):
+    """rbl_tune_cells: time the given system (host arrays x, v [N][3], tag order) at
+    cells_per_cutoff K = 1, 2, 3 and return (fastest K, [ms per step for K = 1, 2, 3],
+    -1 where a K does not apply).  The workspace is allocated here, as for a context;
+    other keyword arguments are make_params's."""
+    import torch
+
+    lib = load()
+    kw.pop("cells_per_cutoff", None)
+    prm = make_params(L, r_c, r_s, skin, p, dt, **kw)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    N = int(x.shape[0])
+    size = ctypes.c_size_t()
+    st = lib.rbl_tune_cells_workspace_size(ctypes.byref(prm), N, ctypes.byref(size))
+    if st != 0:
+        raise RblError(st, lib.rbl_status_string(st).decode())
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    strm = stream if stream is not None else torch.cuda.Stream(dev)
+    ws = torch.empty(int(size.value) + 256, dtype=torch.uint8, device=dev)
+    aligned = (ws.data_ptr() + 255) & ~255
+    K = ctypes.c_int()
+    ms = (ctypes.c_float * 3)()
+    st = lib.rbl_tune_cells(ctypes.byref(prm), N, _ptr(x), _ptr(v), ctypes.c_void_p(aligned), int(size.value),
+                            ctypes.c_void_p(strm.cuda_stream), int(steps), ctypes.byref(K), ms)
+    if st != 0:
+        raise RblError(st, lib.rbl_status_string(st).decode())
+    return K.value, [float(t) for t in ms]
 
 
 def _ptr(a):
