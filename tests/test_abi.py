@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2105_04884_gb300 import _build, rbl
@@ -153,3 +154,26 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(value) == expect, (name, field, value, expect)
         seen += 1
     assert seen == 2 + len(rbl.rbl_params._fields_) + len(rbl.rbl_obs._fields_)
+
+
+def test_tune_cells_workspace_size(lib):
+    """The cell-size tuner's workspace is the largest of the three per-K workspaces
+    (whatever K the parameters carry), and invalid parameters are refused; the tuner
+    itself refuses missing arrays and a step count below 1 before touching a GPU."""
+    base = dict(L=[12.0, 13.0, 20.0], r_c=1.5, r_s=3.5, skin=0.3, p=10, dt=0.005)
+    sizes = [_size(rbl.make_params(cells_per_cutoff=k, **base), 3000) for k in (1, 2, 3)]
+    assert all(st == 0 for st, _ in sizes)
+    for k in (1, 2, 3):
+        s = ctypes.c_size_t()
+        assert lib.rbl_tune_cells_workspace_size(ctypes.byref(rbl.make_params(cells_per_cutoff=k, **base)), 3000,
+                                                 ctypes.byref(s)) == 0
+        assert s.value == max(n for _, n in sizes)
+    s = ctypes.c_size_t()
+    bad = rbl.make_params(**dict(base, r_c=3.5, r_s=1.5))
+    assert lib.rbl_tune_cells_workspace_size(ctypes.byref(bad), 3000, ctypes.byref(s)) == 1
+    K = ctypes.c_int()
+    prm = rbl.make_params(**base)
+    x = np.zeros((3000, 3))
+    assert lib.rbl_tune_cells(ctypes.byref(prm), 3000, None, None, None, 0, None, 10, ctypes.byref(K), None) == 1
+    assert lib.rbl_tune_cells(ctypes.byref(prm), 3000, x.ctypes.data_as(ctypes.c_void_p), None,
+                              ctypes.c_void_p(256), 1 << 30, None, 0, ctypes.byref(K), None) == 1
