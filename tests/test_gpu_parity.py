@@ -45,6 +45,9 @@ CASES = {
                         L=(10.0, 12.5, 20.0)),
     "n1500_aniso_K3": dict(N=1500, rho=0.8, jitter=0.15, rc=1.5, rs=3.5, skin=0.3, p=10, K=3, seed=9,
                            L=(8.2, 11.0, 20.8)),
+    # K = 1 in the first non-cubic box: 2 x 3 x 5 cells, every x cell once
+    "n2000_aniso_K1": dict(N=2000, rho=0.8, jitter=0.15, rc=1.5, rs=3.5, skin=0.3, p=10, K=1, seed=10,
+                           L=(10.0, 12.5, 20.0)),
 }
 
 
