@@ -47,6 +47,11 @@ def test_nve_trajectory_fp64(full_list):
     assert np.abs(_min_image(xg - xo, L)).max() < 1e-9
     assert np.abs(vg - vo).max() < 1e-8
     assert abs(obs["U_est"] - stats[0]) < 1e-8 * abs(stats[0])
+    # the observables launch's kinetic sums against the oracle's own velocities
+    Ko = 0.5 * float((vo * vo).sum())
+    assert abs(obs["K"] - Ko) < 1e-8 * Ko
+    assert abs(obs["T_kin"] - 2 * Ko / (3 * len(xo))) < 1e-8 * obs["T_kin"]
+    assert np.abs(np.asarray(obs["net_momentum"]) - vo.sum(0)).max() < 1e-7
 
 
 @pytest.mark.parametrize("precision", [rbl.RBL_FP64, rbl.RBL_FP32])
