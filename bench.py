@@ -174,6 +174,22 @@ class Clocks:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def step_roofline(alg_force, alg_build, N, ms_step, long_steps, ms_long, long_rebuilds, peak, world):
+    """The fused step's algorithmic bytes per particle-step (alg_force - 24 + 96 + 16)
+    and the list build's per-rebuild bytes amortised over the rebuild interval, against
+    the HBM peak, for the timed K steps and the steady-state run."""
+    step_bytes = alg_force - 24 + 96 + 16
+    interval = long_steps / max(long_rebuilds, 1)
+    amort = alg_build / interval
+    out = {"algorithmic_bytes_per_particle_step": step_bytes, "rebuild_interval_steps": interval,
+           "rebuild_bytes_amortised_per_step": amort, "peak": peak, "unit": "GB/s"}
+    for key, ms in (("timed", ms_step), ("steady_state", ms_long / long_steps)):
+        achieved = (step_bytes + amort) * N / (ms * 1e-3) / 1e9
+        out[key] = {"ms_per_step": ms, "achieved": achieved, "frac": achieved / peak}
+    out["ceiling_particle_steps_per_s"] = peak * 1e9 / (step_bytes + amort) * world
+    return out
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -774,6 +790,17 @@ def run_ours(a, rank, world, local):
         "rows": {"core_mean": nc, "shell_mean": ns, "core_max": obs["Nc_max"], "shell_max": obs["Ns_max"],
                  "stencil_mean": obs["Mc_mean"]},
         "roofline": dominant,
+        # the whole step against the same peak: the method's bytes per particle-step
+        # (force kernel K4 without its own force write, the FP64 x and v read and written
+        # 96, the fixed-point image written 16) plus the list build's bytes amortised over
+        # the steady-state rebuild interval
+        "step_roofline": step_roofline(alg_force, alg_build, N, ms / a.steps, LONG, ms_long,
+                                       obs_long["n_rebuild"] - obs_post["n_rebuild"], peak, world),
+        # pair terms the force kernel evaluates per particle-step: the whole core row
+        # (r < r_c + skin at the build) and the p sampled shell entries
+        "pairs": {"pair_terms_per_particle_step": nc + p,
+                  "pair_terms_per_s": (nc + p) * N * world / t_force,
+                  "pair_flops_per_s_approx": 20.0 * (nc + p) * N * world / t_force},
         "rooflines": {"k_build_culled": roof_build, "k_force": roof_force},
         "clocks": clk,
         "launch_config": tuned,
