@@ -111,3 +111,28 @@ def test_traffic_figure_only_for_matching_sources(tmp_path, monkeypatch):
     assert bench.load_traffic(1000) is None
     # the measured peak, else the documented fallback
     assert bench.load_peaks()[1] == "fallback" and bench.load_peaks()[0] == 6800.0
+
+
+def test_step_roofline_arithmetic():
+    """The whole step's bytes: the force kernel's algorithmic bytes without its force
+    write (24), plus the FP64 x and v read and written (96) and the image written (16),
+    plus the list build's bytes over the rebuild interval; the fraction is the bytes moved
+    per second over the peak, and two ranks double the ceiling."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    nc, p, ns, N = 17.5, 10, 177.0, 1 << 20
+    alg_force = 16 + 4 * nc + 4 + 4 * p + 24
+    alg_build = 16 + 4 * (nc + ns)
+    r = bench.step_roofline(alg_force, alg_build, N, 0.5, 1000, 500.0, 200, 6693.8, 1)
+    assert r["algorithmic_bytes_per_particle_step"] == pytest.approx(16 + 4 * nc + 4 + 4 * p + 96 + 16)
+    assert r["rebuild_interval_steps"] == pytest.approx(5.0)
+    assert r["rebuild_bytes_amortised_per_step"] == pytest.approx(alg_build / 5.0)
+    per_step = r["algorithmic_bytes_per_particle_step"] + r["rebuild_bytes_amortised_per_step"]
+    assert r["timed"]["achieved"] == pytest.approx(per_step * N / 0.5e-3 / 1e9)
+    assert r["steady_state"]["frac"] == pytest.approx(per_step * N / 0.5e-3 / 1e9 / 6693.8)
+    r2 = bench.step_roofline(alg_force, alg_build, N, 0.5, 1000, 500.0, 200, 6693.8, 2)
+    assert r2["ceiling_particle_steps_per_s"] == pytest.approx(2 * r["ceiling_particle_steps_per_s"])
+    assert bench.step_roofline(alg_force, alg_build, N, 0.5, 10, 5.0, 0, 6693.8, 1)["rebuild_interval_steps"] == 10
