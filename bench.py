@@ -727,6 +727,15 @@ def run_ours(a, rank, world, local):
     clk = clocks.stop()
     clk["window"] = "the %d timed steps and the %d-step steady-state run right after them" % (a.steps, LONG)
     obs_long = s.observables()
+    # the list build timed on forced rebuilds of the equilibrated state (the phase-timed
+    # steps' list-build phase also carries the build's skipped launches on the steps that
+    # do not rebuild)
+    s.set_phase_timing(True)
+    s.rebuild_times(reset=True)
+    for _ in range(4):
+        s.build_lists()
+    (rb_sort, rb_lists), rb_n = s.rebuild_times()
+    s.set_phase_timing(False)
     obs = obs_post
     value = whole_job_rate(N, a.steps, world, ms)
     rebuilds = obs["n_rebuild"] - obs_pre["n_rebuild"]
@@ -751,18 +760,22 @@ def run_ours(a, rank, world, local):
         roof_force["traffic_frac"] = traffic_f / t_force / 1e9 / peak
     # Roofline of the list build (K3), per rebuild: own position 16 and the rows, core
     # and shell, as 4-byte entries 4 (n_c + N_s) (~800 B per particle per rebuild).
-    # Its launches inside the phase-timed steps that did not rebuild return at once;
-    # the phase total is divided by the rebuilds (a slight overestimate of the
-    # per-rebuild time).
+    # Timed on forced rebuilds of the equilibrated state; the step phases' figure (the
+    # phase total over the rebuilds, which also carries the build's launches on the
+    # phase-timed steps that do not rebuild) is reported beside it.
     alg_build = 16 + 4 * (nc + ns)
-    t_build = ph["list_build"] * nsteps / max(rebuilds_phase, 1) * 1e-3
+    t_build_phase = ph["list_build"] * nsteps / max(rebuilds_phase, 1) * 1e-3
+    t_build = rb_lists / rb_n * 1e-3
     traffic_b = load_traffic(N, "list_build_traffic.json")
     roof_build = {"kernel": "k_build_culled<0> (bounding-box cull into the cell's candidate table, then core row + "
                             "shell mask; one warp per home cell)", "bound": "hbm",
                   "achieved": alg_build * N / t_build / 1e9, "peak": peak, "unit": "GB/s",
                   "frac": alg_build * N / t_build / 1e9 / peak, "peak_source": peak_kind,
                   "algorithmic_bytes_per_particle": alg_build, "traffic": traffic_b, "traffic_per": "launch",
-                  "ms_per_launch": t_build * 1e3, "launches_timed": rebuilds_phase,
+                  "ms_per_launch": t_build * 1e3, "launches_timed": rb_n,
+                  "timed_on": "forced rebuilds of the equilibrated state (rbl_build_lists under phase timing)",
+                  "cell_sort_ms_per_rebuild": rb_sort / rb_n,
+                  "ms_per_rebuild_from_step_phases": t_build_phase * 1e3,
                   "share_of_step": ph["list_build"] / sum(ph.values())}
     dominant = roof_build if ph["list_build"] >= ph["force_kernel"] else roof_force
     result = {

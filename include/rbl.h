@@ -336,6 +336,13 @@ rbl_status rbl_tune_cells(const rbl_params *prm, int N, const double *x, const d
 rbl_status rbl_set_phase_timing(rbl_ctx *ctx, int enable);
 rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[5], long long *steps, int reset);
 
+/* With phase timing enabled, every rebuild made outside the step loop (rbl_build_lists,
+ * and the first force evaluation after a new state) is timed on its own: ms[0] the cell
+ * sort chain, ms[1] the list build, summed over *rebuilds such rebuilds (host pointers;
+ * either may be NULL).  These carry none of the skipped rebuild launches that the
+ * phase-timed steps which do not rebuild make.  reset = 1 clears the sums after reading. */
+rbl_status rbl_rebuild_times(rbl_ctx *ctx, double ms[2], long long *rebuilds, int reset);
+
 /* Allocation-free force evaluation (the paper has no counterpart; this is a service
  * for callers that may not allocate).  Some callers cannot allocate device memory
  * when they need forces: a plugin called inside another engine's time step whose

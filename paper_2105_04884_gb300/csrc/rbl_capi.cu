@@ -405,7 +405,26 @@ rbl_status check_flags(rbl_ctx *ctx, bool replicas = false)
 rbl_status ensure_lists(rbl_ctx *ctx)
 {
     if (ctx->lists_valid) return RBL_OK;
-    CK(launch_rebuild(ctx->view, ctx->n_scan_blocks, false, ctx->stream));
+    if (ctx->phase_timing) {
+        // a rebuild outside the step loop, timed on its own: the sort chain and the list
+        // build, with none of the skipped launches of the steps that do not rebuild
+        for (int k = 0; k < 3; ++k)
+            if (!ctx->rb_ev[k]) CK(cudaEventCreate(&ctx->rb_ev[k]));
+        CK(cudaEventRecord(ctx->rb_ev[0], ctx->stream));
+        CK(launch_rebuild_sort(ctx->view, ctx->n_scan_blocks, false, ctx->stream));
+        CK(cudaEventRecord(ctx->rb_ev[1], ctx->stream));
+        CK(launch_rebuild_lists(ctx->view, false, ctx->stream));
+        CK(cudaEventRecord(ctx->rb_ev[2], ctx->stream));
+        CK(cudaEventSynchronize(ctx->rb_ev[2]));
+        for (int k = 0; k < 2; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->rb_ev[k], ctx->rb_ev[k + 1]));
+            ctx->rebuild_ms[k] += ms;
+        }
+        ctx->rebuild_n += 1;
+    } else {
+        CK(launch_rebuild(ctx->view, ctx->n_scan_blocks, false, ctx->stream));
+    }
     ctx->lists_valid = 1;
     ctx->force_valid = 0;
     return RBL_OK;
@@ -1426,12 +1445,27 @@ rbl_status rbl_phase_times(rbl_ctx *ctx, double ms[5], long long *steps, int res
     return RBL_OK;
 }
 
+rbl_status rbl_rebuild_times(rbl_ctx *ctx, double ms[2], long long *rebuilds, int reset)
+{
+    if (!ctx) return RBL_EINVAL;
+    if (ms)
+        for (int k = 0; k < 2; ++k) ms[k] = ctx->rebuild_ms[k];
+    if (rebuilds) *rebuilds = ctx->rebuild_n;
+    if (reset) {
+        ctx->rebuild_ms[0] = ctx->rebuild_ms[1] = 0.0;
+        ctx->rebuild_n = 0;
+    }
+    return RBL_OK;
+}
+
 void rbl_destroy(rbl_ctx *ctx)
 {
     if (!ctx) return;
     drop_graphs(ctx);
     for (int k = 0; k < ctx->ev_cap * kPhaseEvents; ++k) cudaEventDestroy(ctx->ev[k]);
     std::free(ctx->ev);
+    for (int k = 0; k < 3; ++k)
+        if (ctx->rb_ev[k]) cudaEventDestroy(ctx->rb_ev[k]);
     delete ctx->h_sc;
     delete[] ctx->h_rs;
     delete[] ctx->h_box;

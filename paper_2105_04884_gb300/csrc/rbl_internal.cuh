@@ -614,6 +614,9 @@ struct rbl_ctx {
     int ev_cap;                 // steps the event pool covers
     double phase_ms[5];
     long long phase_steps;
+    double rebuild_ms[2];       // phase timing: forced rebuilds' cell sort chain and list build
+    long long rebuild_n;        // forced rebuilds timed
+    cudaEvent_t rb_ev[3];       // their events (created on first use)
     char err[512];
     rbl::DevScalars *h_sc;      // host mirror of the device scalars
     rbl::RepScalars *h_rs;      // host mirror of the per-replica scalars [R]

@@ -66,7 +66,7 @@ EXPORTS = ["rbl_params_default", "rbl_workspace_size", "rbl_workspace_size_batch
            "rbl_rdf", "rbl_density_profile", "rbl_set_launch_config", "rbl_autotune", "rbl_set_phase_timing",
            "rbl_phase_times", "rbl_forces_static", "rbl_checkpoint_size", "rbl_save_checkpoint",
            "rbl_load_checkpoint", "rbl_destroy", "rbl_last_error", "rbl_status_string",
-           "rbl_tune_cells_workspace_size", "rbl_tune_cells"]
+           "rbl_tune_cells_workspace_size", "rbl_tune_cells", "rbl_rebuild_times"]
 
 _lib = None
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = False):
     L.rbl_autotune.argtypes = [P, I, P, P]
     L.rbl_set_phase_timing.argtypes = [P, I]
     L.rbl_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
+    L.rbl_rebuild_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL), I]
     L.rbl_forces_static.argtypes = [ctypes.POINTER(rbl_params), I, P, LL, P, P]
     L.rbl_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.rbl_save_checkpoint.argtypes = [P, P, I]
@@ -387,6 +388,14 @@ class _Context:
 
     def set_phase_timing(self, enable=True):
         self._check(self.lib.rbl_set_phase_timing(self.h, int(bool(enable))))
+
+    def rebuild_times(self, reset=False):
+        """(ms [cell sort chain, list build] summed over the rebuilds timed outside the
+        step loop, their number)."""
+        ms = (ctypes.c_double * 2)()
+        n = ctypes.c_longlong()
+        self._check(self.lib.rbl_rebuild_times(self.h, ms, ctypes.byref(n), int(bool(reset))))
+        return list(ms), n.value
 
     def phase_times(self, reset=False):
         """(ms per phase [integrate, cell sort, list build, force kernel, force reduction],
