@@ -777,6 +777,8 @@ def run_ours(a, rank, world, local):
                   "cell_sort_ms_per_rebuild": rb_sort / rb_n,
                   "ms_per_rebuild_from_step_phases": t_build_phase * 1e3,
                   "share_of_step": ph["list_build"] / sum(ph.values())}
+    if traffic_b is not None:
+        roof_build["traffic_frac"] = traffic_b / t_build / 1e9 / peak
     dominant = roof_build if ph["list_build"] >= ph["force_kernel"] else roof_force
     result = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": a.steps,
