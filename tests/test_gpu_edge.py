@@ -1,0 +1,158 @@
+"""Degenerate inputs on the GPU against the oracle, through the C ABI (Sec. 2, Algorithm 1).
+
+- the smallest system the library takes, N = 2: one pair inside the core, inside the
+  shell, in the skin band beyond r_s, beyond r_s + skin (no neighbour at all: empty
+  rows, no batch, a force of exactly zero), and a core pair through the periodic face;
+- two small clusters in a large box, one of them split by the box corner, so that
+  nearly every cell is empty and the cell stencils wrap (the local density is passed
+  as rho_cap, which sizes the candidate tables);
+- particles exactly on the box faces: coordinates 0 and the largest double below L,
+  whose fixed-point image rounds to 2^32, i.e. 0 (R10's image of a periodic box).
+
+Each case: core, shell and full rows and the batches at two steps bit-exact; forces
+within 1e-12 (FP64 path) and 1e-5 (FP32 path) of the oracle's in relative global norm
+(exactly zero where the oracle's are); a 30-step FP64 velocity-Verlet trajectory within
+1e-9 of the oracle's, with the same number of list builds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_04884_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2105_04884_gb300 import rbl  # noqa: E402
+
+RC, RS, SKIN, P, DT = 1.5, 3.5, 0.3, 10, 0.005
+
+
+def _pair(d, face=False):
+    """Two particles at distance d along the body diagonal (or, face=True, along x
+    through the periodic face), in a box of 10, with opposite velocities."""
+    L = np.full(3, 10.0)
+    u = np.ones(3) / np.sqrt(3.0)
+    if face:
+        x = np.array([[0.3, 5.0, 5.0], [10.0 - (d - 0.3), 5.0, 5.0]])
+    else:
+        x = np.array([[2.0, 3.0, 4.0], [2.0, 3.0, 4.0] + d * u])
+    v = np.array([[0.5, -0.2, 0.1], [-0.5, 0.2, -0.1]])
+    return x, v, L, {}
+
+
+def _clusters():
+    """Two 4 x 4 x 4 simple-cubic clusters (spacing 1.12, jitter 0.05) in a box of 25:
+    one in the middle, one around the box corner."""
+    g = np.stack(np.meshgrid(*[np.arange(4) * 1.12] * 3, indexing="ij"), -1).reshape(-1, 3) - 1.68
+    rng = np.random.default_rng(12)
+    L = np.full(3, 25.0)
+    x = np.concatenate([g + 12.5, g]) + rng.uniform(-0.05, 0.05, (128, 3))
+    x = np.mod(x, L)
+    v = inputs.maxwell_boltzmann(128, 0.3, seed=12)
+    return x, v, L, {"rho_cap": 1.0}
+
+
+def _faces():
+    """FCC (N = 500, rho* = 0.8) moved so that lattice planes lie on the faces; of the
+    particles within 0.06 of a face, every other one is put exactly on it: at 0 on the
+    low side, at the largest double below L on the high side."""
+    x, L = inputs.fcc(500, 0.8, 0.05, seed=11)
+    x = np.mod(x - L / 5 / 4, L)
+    for a in range(3):
+        lo = np.nonzero(x[:, a] < 0.06)[0][::2]
+        hi = np.nonzero(x[:, a] > L[a] - 0.06)[0][::2]
+        assert len(lo) > 0 and len(hi) > 0
+        x[lo, a] = 0.0
+        x[hi, a] = np.nextafter(L[a], 0.0)
+    v = inputs.maxwell_boltzmann(500, 1.5, seed=11)
+    return x, v, L, {}
+
+
+CASES = {
+    "pair_core": lambda: _pair(1.2),
+    "pair_shell": lambda: _pair(2.5),
+    "pair_skin_band": lambda: _pair(3.65),
+    "pair_beyond": lambda: _pair(4.5),
+    "pair_core_through_face": lambda: _pair(1.2, face=True),
+    "clusters_empty_cells": _clusters,
+    "particles_on_faces": _faces,
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    x, v, L, kw = CASES[request.param]()
+    lists = oracle.build_lists(x, L, RC, RS, SKIN, K=2, method="cells")
+    return request.param, x, v, L, kw, lists
+
+
+def _system(x, v, L, kw, **more):
+    args = dict(T=1.0, gamma=0.0, seed=3, cells_per_cutoff=2)
+    args.update(kw)
+    args.update(more)
+    return rbl.System(x, v, L, RC, RS, SKIN, P, DT, **args)
+
+
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def test_lists_bit_exact(case):
+    name, x, v, L, kw, lists = case
+    s = _system(x, v, L, kw)
+    for kind, row in ((0, "core"), (1, "shell")):
+        rows, counts = s.get_lists(kind)
+        assert np.array_equal(counts, getattr(lists, "n_" + row)), (name, row)
+        for i in range(len(x)):
+            assert np.array_equal(rows[i, : counts[i]], lists.row(row, i)), (name, row, i)
+    f = _system(x, v, L, kw, full_list=True)
+    rows, counts = f.get_lists(1)
+    assert np.array_equal(counts, lists.n_full), name
+    for i in range(len(x)):
+        assert np.array_equal(rows[i, : counts[i]], lists.row("full", i)), (name, i)
+    if name == "pair_beyond":
+        assert counts.sum() == 0 and lists.n_core.sum() == 0
+
+
+@pytest.mark.parametrize("step", [0, 5])
+def test_batches_bit_exact(case, step):
+    name, x, v, L, kw, lists = case
+    s = _system(x, v, L, kw)
+    batch, counts = s.get_batch(step)
+    _, _, ob, obn = oracle.rbl_forces(x, L, RC, RS, SKIN, P, 3, step, lists, want_batch=True)
+    assert np.array_equal(counts, obn), name
+    for i in range(len(x)):
+        assert np.array_equal(batch[i, : counts[i]], ob[i, : obn[i]]), (name, i)
+
+
+@pytest.mark.parametrize("precision,tol", [(rbl.RBL_FP64, 1e-12), (rbl.RBL_FP32, 1e-5)])
+def test_forces(case, precision, tol):
+    name, x, v, L, kw, lists = case
+    s = _system(x, v, L, kw, precision=precision)
+    F = s.forces()
+    Fo, _, _, _ = oracle.rbl_forces(x, L, RC, RS, SKIN, P, 3, 0, lists)
+    Fo = oracle.subtract_mean(Fo)
+    norm = np.linalg.norm(Fo)
+    if norm == 0.0:
+        assert not F.any(), name
+    else:
+        assert np.linalg.norm(F - Fo) <= tol * norm, name
+
+
+def test_trajectory_fp64(case):
+    name, x, v, L, kw, lists = case
+    n = 30
+    s = _system(x, v, L, kw, precision=rbl.RBL_FP64)
+    s.step(n)
+    xg, vg, step = s.get_state()
+    obs = s.observables()
+    xo, vo, _, stats = oracle.run(x, v, L, RC, RS, SKIN, P, DT, 1.0, 0.0, 3, n)
+    assert step == n
+    assert obs["n_rebuild"] == int(stats[2]), name
+    assert np.abs(_min_image(xg - xo, L)).max() < 1e-9, name
+    assert np.abs(vg - vo).max() < 1e-8, name
+    assert (xg >= 0.0).all() and (xg < L).all(), name
