@@ -7,7 +7,8 @@
   nearly every cell is empty and the cell stencils wrap (the local density is passed
   as rho_cap, which sizes the candidate tables);
 - particles exactly on the box faces: coordinates 0 and the largest double below L,
-  whose fixed-point image rounds to 2^32, i.e. 0 (R10's image of a periodic box).
+  whose fixed-point image rounds to 2^32, i.e. 0 (R10's image of a periodic box);
+- the largest batch, p = 128, below every shell size of a dense fluid.
 
 Each case: core, shell and full rows and the batches at two steps bit-exact; forces
 within 1e-12 (FP64 path) and 1e-5 (FP32 path) of the oracle's in relative global norm
@@ -156,3 +157,25 @@ def test_trajectory_fp64(case):
     assert np.abs(_min_image(xg - xo, L)).max() < 1e-9, name
     assert np.abs(vg - vo).max() < 1e-8, name
     assert (xg >= 0.0).all() and (xg < L).all(), name
+
+
+@pytest.mark.parametrize("precision,tol", [(rbl.RBL_FP64, 1e-12), (rbl.RBL_FP32, 1e-5)])
+def test_largest_batch(precision, tol):
+    """p = 128, the largest batch, below the shell sizes of a dense fluid (N_s ~ 177):
+    batches bit-exact at two steps, forces at the bars."""
+    p = 128
+    x, L = inputs.fcc(2000, 0.8, 0.05, seed=13)
+    v = inputs.maxwell_boltzmann(2000, 1.5, seed=13)
+    lists = oracle.build_lists(x, L, RC, RS, SKIN, K=2, method="cells")
+    assert lists.n_shell.min() > p
+    s = rbl.System(x, v, L, RC, RS, SKIN, p, DT, T=1.5, seed=13, precision=precision)
+    for step in (0, 7):
+        batch, counts = s.get_batch(step)
+        _, _, ob, obn = oracle.rbl_forces(x, L, RC, RS, SKIN, p, 13, step, lists, want_batch=True)
+        assert np.array_equal(counts, obn) and (counts == p).all()
+        for i in range(len(x)):
+            assert np.array_equal(batch[i], ob[i]), (step, i)
+    F = s.forces()
+    Fo, _, _, _ = oracle.rbl_forces(x, L, RC, RS, SKIN, p, 13, 0, lists)
+    Fo = oracle.subtract_mean(Fo)
+    assert np.linalg.norm(F - Fo) <= tol * np.linalg.norm(Fo)
