@@ -8,7 +8,8 @@
   as rho_cap, which sizes the candidate tables);
 - particles exactly on the box faces: coordinates 0 and the largest double below L,
   whose fixed-point image rounds to 2^32, i.e. 0 (R10's image of a periodic box);
-- the largest batch, p = 128, below every shell size of a dense fluid.
+- the largest batch, p = 128, below every shell size of a dense fluid;
+- all of these as the replicas of one ensemble, against each run on its own.
 
 Each case: core, shell and full rows and the batches at two steps bit-exact; forces
 within 1e-12 (FP64 path) and 1e-5 (FP32 path) of the oracle's in relative global norm
@@ -179,3 +180,28 @@ def test_largest_batch(precision, tol):
     Fo, _, _, _ = oracle.rbl_forces(x, L, RC, RS, SKIN, p, 13, 0, lists)
     Fo = oracle.subtract_mean(Fo)
     assert np.linalg.norm(F - Fo) <= tol * np.linalg.norm(Fo)
+
+
+def test_degenerate_replicas_in_one_ensemble():
+    """Every case above as one replica of an ensemble (uneven sizes from 2 to 500,
+    boxes from 8.5 to 25, the local density passed as rho_cap for all): forces and 30
+    FP32 steps bit-identical to each case run as a context of its own."""
+    reps = []
+    for k, name in enumerate(sorted(CASES)):
+        x, v, L, _ = CASES[name]()
+        reps.append(inputs.Replica(len(x), 0.0, 1.0, 3 + k, x, v, L))
+    kw = dict(r_c=RC, r_s=RS, skin=SKIN, p=P, dt=DT, gamma=0.0, rho_cap=1.0)
+    ens = rbl.Ensemble(reps, **kw)
+    F = ens.split(ens.forces())
+    singles = [rbl.System(rp.x, rp.v, rp.L, T=rp.T, seed=rp.seed, **kw) for rp in reps]
+    for r, s in enumerate(singles):
+        assert np.array_equal(F[r], s.forces()), r
+    ens.step(30)
+    x, v, _ = ens.get_state()
+    xs, vs = ens.split(x), ens.split(v)
+    nreb = [o["n_rebuild"] for o in ens.observables()]
+    for r, s in enumerate(singles):
+        s.step(30)
+        x1, v1, _ = s.get_state()
+        assert np.array_equal(xs[r], x1) and np.array_equal(vs[r], v1), r
+        assert nreb[r] == s.observables()["n_rebuild"], r
